@@ -1,0 +1,303 @@
+"""Pins of the oracle's radiative transfer and statistical equilibrium.
+
+What fixes each part (Sect. 2 of the paper for the method):
+  * LTE start (Sect. 3.3.2): rigid-rotor partition function, classical
+    high-temperature expansion.
+  * Line parameters: Kirchhoff (S = Planck occupation in LTE) and the LTE
+    column-density / integrated-opacity relation of radio astronomy.
+  * Rate equations: detailed balance -- collisions alone, radiation alone
+    (J = Planck at T_rad) and both at one temperature give Boltzmann
+    populations for any escape probability beta, in the ALI and in the
+    lambda-iteration form.
+  * Two-level optically thin closed form of the level ratio.
+  * Formal solution / spectra: uniform static sphere I(p) in closed form;
+    optically thin emergent intensity as the sum of emissivities.
+  * Ray simulation: isothermal cloud at T_bg keeps I = n_bg everywhere;
+    cell-averaged mean intensity of a uniform sphere equals the escape-
+    probability closed form; static clouds give NORM = band fraction; a
+    uniform cube crossed along an axis gives closed-form J_ext and beta.
+  * ALI (Sect. 2): same fixed point as lambda iteration, fewer iterations
+    when optically thick; thermalisation at high density.
+Parity unpinned: the infall line shape (qualitative blue asymmetry only).
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+import loc_inputs as LI
+
+H = 6.62607015e-27
+KB = 1.380649e-16
+C = 2.99792458e10
+AMU = 1.66053906660e-24
+
+
+def planck_occ(nu, T):
+    return 1.0 / np.expm1(H * nu / (KB * T))
+
+
+def test_rotor_partition_function(oracle):
+    mol = LI.rotor_molecule(n_levels=400)
+    T = 200.0
+    x = oracle.lte_populations(mol, np.array([T]))[0]
+    theta = H * 57.6e9 / KB
+    Z = T / theta + 1.0 / 3.0 + theta / (15.0 * T) + 4.0 * theta ** 2 / (315.0 * T ** 2)
+    assert x[0] == pytest.approx(1.0 / Z, rel=1e-8)
+    assert x.sum() == pytest.approx(1.0, abs=1e-14)
+
+
+def test_kirchhoff_and_lte_opacity(oracle):
+    mol = LI.rotor_molecule()
+    m = LI.cloud1d_rotor(K=5)
+    x = oracle.lte_populations(mol, m["t_kin"])
+    Kp, S = oracle.line_params(mol, m, x)
+    for t in range(len(mol["line_nu"])):
+        nu, A, u = mol["line_nu"][t], mol["line_A"][t], mol["line_u"][t]
+        np.testing.assert_allclose(S[t], planck_occ(nu, m["t_kin"]), rtol=1e-11)
+        # integrated opacity per unit length and velocity:
+        # int alpha dv = c^3 A / (8 pi nu^3) n_u (exp(h nu / k T) - 1)
+        n_u = m["n_h2"] * m["abundance"] * x[:, u]
+        ref = C ** 3 * A / (8 * np.pi * nu ** 3) * n_u * np.expm1(H * nu / (KB * m["t_kin"]))
+        np.testing.assert_allclose(Kp[t] * m["dv"], ref, rtol=1e-11)
+
+
+def _se_inputs(mol, n_cells, J, beta):
+    """SIJ/ESC/NORM giving J_ext = J and escape probability beta."""
+    T = len(mol["line_nu"])
+    NORM = np.full(n_cells, 0.7)
+    SIJ = np.asarray(J).reshape(T, -1) * NORM * np.ones((T, n_cells))
+    ESC = np.asarray(beta).reshape(T, -1) * NORM * np.ones((T, n_cells))
+    return SIJ, ESC, NORM
+
+
+@pytest.mark.parametrize("nlev", [2, 7, 12])
+def test_se_collisions_only_boltzmann(oracle, nlev):
+    mol = LI.rotor_molecule(n_levels=nlev)
+    mol["line_A"] = np.zeros_like(mol["line_A"])
+    m = dict(n_h2=np.array([1e2, 1e4, 1e7]), t_kin=np.array([8.0, 25.0, 60.0]), t_bg=2.73)
+    T = len(mol["line_nu"])
+    SIJ, ESC, NORM = _se_inputs(mol, 3, np.full(T, 0.3), np.full(T, 0.5))
+    x = oracle.se_solve(mol, m, SIJ, ESC, NORM, np.zeros((T, 3)))
+    ref = oracle.lte_populations(mol, m["t_kin"])
+    np.testing.assert_allclose(x, ref, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("ali", [True, False])
+def test_se_radiation_only_boltzmann_at_trad(oracle, ali):
+    mol = LI.rotor_molecule(n_levels=9)
+    T = len(mol["line_nu"])
+    t_rad = 17.0
+    m = dict(n_h2=np.zeros(2), t_kin=np.array([10.0, 40.0]), t_bg=2.73)
+    beta = np.linspace(0.05, 1.0, T)
+    n = planck_occ(mol["line_nu"], t_rad)
+    # J_ext = beta n with local S = n: mean intensity J_ext + S (1 - beta) = n
+    SIJ, ESC, NORM = _se_inputs(mol, 2, beta * n, beta)
+    S = np.repeat(n[:, None], 2, axis=1)
+    x = oracle.se_solve(mol, m, SIJ, ESC, NORM, S, ali=ali)
+    ref = oracle.lte_populations(mol, np.full(2, t_rad))
+    np.testing.assert_allclose(x, ref, rtol=1e-11)
+
+
+@pytest.mark.parametrize("ali", [True, False])
+def test_se_radiation_and_collisions_same_temperature(oracle, ali):
+    mol = LI.rotor_molecule(n_levels=12)
+    T = len(mol["line_nu"])
+    tk = np.array([6.0, 15.0, 33.0])
+    m = dict(n_h2=np.array([3e2, 3e4, 3e6]), t_kin=tk, t_bg=2.73)
+    beta = np.geomspace(1e-3, 1.0, T)[:, None] * np.ones((1, 3))
+    n = planck_occ(mol["line_nu"][:, None], tk[None, :])
+    NORM = np.array([0.9, 1.0, 0.4])
+    SIJ = beta * n * NORM
+    ESC = beta * NORM
+    x = oracle.se_solve(mol, m, SIJ, ESC, NORM, n, ali=ali)
+    np.testing.assert_allclose(x, oracle.lte_populations(mol, tk), rtol=1e-10)
+
+
+def test_two_level_thin_closed_form(oracle):
+    mol = LI.two_level_molecule()
+    m = LI.cloud1d_two_level(abundance=1e-15)       # tau ~ 1e-7
+    x, _ = oracle.iterate_1d(mol, m, 3)
+    A, gu, gl = mol["line_A"][0], mol["g"][1], mol["g"][0]
+    nbg = planck_occ(mol["line_nu"][0], m["t_bg"])
+    cul = m["n_h2"] * mol["coll_k"][0]
+    clu = cul * (gu / gl) * np.exp(-mol["energy_K"][1] / m["t_kin"])
+    # out-of-band loss: J_ext = n_bg but the profile fraction is inside NORM,
+    # so the thin limit is exact for the ratio
+    ratio = (clu + (gu / gl) * A * nbg) / (cul + A * (1.0 + nbg))
+    np.testing.assert_allclose(x[:, 1] / x[:, 0], ratio, rtol=1e-6)
+
+
+def test_uniform_sphere_spectrum_closed_form(oracle):
+    mol = LI.two_level_molecule()
+    m = LI.uniform_sphere(K=7, n_ch=32, abundance=2e-8)
+    rng = np.random.default_rng(3)
+    x = np.tile(np.array([0.4, 0.6]), (7, 1))
+    R = m["radius"][-1]
+    p = np.concatenate([[0.0], rng.uniform(0, R, 6), [1.01 * R]])
+    T = oracle.spectra_1d(mol, m, x, 0, p)
+    Kp, S = oracle.line_params(mol, m, x)
+    sig = np.sqrt(m["sigma_turb"][0] ** 2 + KB * m["t_kin"][0] / (mol["mass_amu"] * AMU))
+    phi = oracle.profile(m["n_ch"], m["v_min"], m["dv"], 0.0, sig)
+    nu = mol["line_nu"][0]
+    nbg = planck_occ(nu, m["t_bg"])
+    for ip, pp in enumerate(p):
+        L = 2.0 * np.sqrt(max(R * R - pp * pp, 0.0))
+        tau = Kp[0, 0] * phi * L
+        n = nbg * np.exp(-tau) - S[0, 0] * np.expm1(-tau)
+        np.testing.assert_allclose(T[ip], H * nu / KB * (n - nbg), rtol=1e-11, atol=1e-13)
+
+
+def test_thin_emergent_intensity_is_sum_of_emissivities(oracle):
+    mol = LI.two_level_molecule()
+    m = LI.cloud1d_two_level(K=12, abundance=1e-17)
+    x, _ = oracle.iterate_1d(mol, m, 2)
+    Kp, S = oracle.line_params(mol, m, x)
+    nu = mol["line_nu"][0]
+    nbg = planck_occ(nu, m["t_bg"])
+    R = m["radius"]
+    for j in (0, 5, 11):
+        cell, s, cosv = oracle.paths_1d(m, j)
+        p = (j + 0.5) * R[-1] / m["n_rays"]
+        T = oracle.spectra_1d(mol, m, x, 0, [p])[0]
+        acc = np.zeros(m["n_ch"])
+        for c, ss, cv in zip(cell, s, cosv):
+            sig = np.sqrt(m["sigma_turb"][c] ** 2 + KB * m["t_kin"][c] / (mol["mass_amu"] * AMU))
+            phi = oracle.profile(m["n_ch"], m["v_min"], m["dv"], m["v"][c] * cv, sig)
+            acc += Kp[0, c] * phi * ss * (S[0, c] - nbg)
+        # error of the thin limit is O(tau_total) relative
+        tau_tot = sum(Kp[0, c] * ss for c, ss in zip(cell, s)) * 0.2
+        assert tau_tot < 1e-6
+        # atol: T = (h nu / k)(n - n_bg) cancels against n_bg ~ 0.26 in FP64
+        np.testing.assert_allclose(T, H * nu / KB * acc, rtol=3 * tau_tot, atol=1e-14)
+
+
+def test_isothermal_at_background_keeps_intensity(oracle):
+    """S = n_bg in every cell: the field stays n_bg, so the mean intensity
+    J_ext + S (1 - beta) equals n_bg in every cell for any velocity field."""
+    mol = LI.rotor_molecule(n_levels=6)
+    m = LI.cloud1d_rotor(K=20, n_ch=48, abundance=1e-4)
+    m["t_kin"] = np.full(20, m["t_bg"])
+    x = oracle.lte_populations(mol, m["t_kin"])
+    Kp, S = oracle.line_params(mol, m, x)
+    SIJ, ESC, NORM = oracle.march_1d(mol, m, Kp, S)
+    Jbar = (SIJ + S * (NORM - ESC)) / NORM
+    nbg = planck_occ(mol["line_nu"], m["t_bg"])[:, None]
+    np.testing.assert_allclose(Jbar, np.broadcast_to(nbg, Jbar.shape), rtol=1e-12)
+    assert (Kp.max() * m["radius"][0]) > 1.0        # genuinely thick
+
+
+def _beta_sphere(tau_R):
+    """Mean escape probability of a uniform sphere of radius optical depth
+    tau_R, by direct quadrature of its definition (volume and angle average
+    of exp(-tau * distance to the surface / R))."""
+    f = lambda mu, r: 1.5 * r * r * np.exp(-tau_R * (-r * mu + np.sqrt(1 - r * r * (1 - mu * mu))))
+    return integrate.dblquad(f, 0, 1, -1, 1, epsabs=1e-13, epsrel=1e-12)[0]
+
+
+def test_sphere_mean_intensity_matches_escape_probability(oracle):
+    mol = LI.two_level_molecule()
+    errs = []
+    for n_rays in (1000, 8000):
+        m = LI.uniform_sphere(K=4, n_ch=12, n_rays=n_rays, abundance=3e-8, half_width_kms=1.0)
+        x = oracle.lte_populations(mol, m["t_kin"])
+        Kp, S = oracle.line_params(mol, m, x)
+        SIJ, ESC, NORM = oracle.march_1d(mol, m, Kp, S)
+        W = oracle.weights_1d(m)
+        sig = np.sqrt(m["sigma_turb"][0] ** 2 + KB * m["t_kin"][0] / (mol["mass_amu"] * AMU))
+        phi = oracle.profile(m["n_ch"], m["v_min"], m["dv"], 0.0, sig)
+        b = np.array([_beta_sphere(Kp[0, 0] * ph * m["radius"][-1]) for ph in phi])
+        nbg = planck_occ(mol["line_nu"][0], m["t_bg"])
+        exact = (phi * (S[0, 0] * (1 - b) + nbg * b)).sum() / phi.sum()
+        Jbar = (SIJ[0] + S[0] * (NORM - ESC[0])) / NORM
+        errs.append(abs((W * Jbar).sum() / W.sum() / exact - 1.0))
+        np.testing.assert_allclose(NORM, phi.sum(), rtol=1e-13)     # static: band fraction
+    assert errs[1] < 1e-6
+    assert errs[1] < errs[0] / 4
+
+
+def test_ali_and_lambda_iteration_same_fixed_point(oracle):
+    mol = LI.two_level_molecule()
+    m = LI.cloud1d_two_level(K=16, abundance=1e-7)
+    xa, da = oracle.iterate_1d(mol, m, 400, ali=True)
+    xl, dl = oracle.iterate_1d(mol, m, 1500, ali=False)
+    np.testing.assert_allclose(oracle.tex(mol, xa), oracle.tex(mol, xl), rtol=1e-9)
+    # optically thick: ALI converges in fewer iterations (Sect. 2)
+    assert np.argmax(da < 1e-5) * 1.5 < np.argmax(dl < 1e-5)
+
+
+def test_high_density_thermalises(oracle):
+    mol = LI.rotor_molecule()
+    m = LI.cloud1d_rotor(K=24, n_ch=64, density_scale=1e9)
+    x, d = oracle.iterate_1d(mol, m, 8)
+    # departures from LTE are of order A_ul / C_ul (< 2e-5 here)
+    bound = mol["line_A"].max() / (m["n_h2"].min() * mol["coll_k"].max())
+    assert bound < 2e-5
+    np.testing.assert_allclose(x, oracle.lte_populations(mol, m["t_kin"]), rtol=5 * bound)
+
+
+def test_infall_blue_asymmetry_qualitative(oracle):
+    """Parity unpinned: only the sign of the classic infall signature."""
+    mol = LI.two_level_molecule()
+    m = LI.cloud1d_two_level(abundance=1e-8)
+    x, _ = oracle.iterate_1d(mol, m, 60)
+    T = oracle.spectra_1d(mol, m, x, 0, [0.0])[0]
+    vc = m["v_min"] + (np.arange(m["n_ch"]) + 0.5) * m["dv"]
+    blue = T[(vc < 0) & (vc > -1.5e5)].max()
+    red = T[(vc > 0) & (vc < 1.5e5)].max()
+    assert blue > red
+
+
+def test_3d_slab_along_axis_closed_form(oracle):
+    """Uniform static cube crossed along +z (or -z): the intensity entering
+    cell iz is n_bg e^{-iz tau1} + S (1 - e^{-iz tau1}), so J_ext and beta
+    of every cell follow in closed form."""
+    mol = LI.two_level_molecule()
+    N = 4
+    g = LI.small_grid3d(N=N, n_ch=16)
+    nc = N ** 3
+    for key in ("n_h2",):
+        g[key] = np.full(nc, 3e4)
+    for key in ("vx", "vy", "vz"):
+        g[key] = np.zeros(nc)
+    g["abundance"] = np.full(nc, 1e-8)
+    g["t_kin"] = np.full(nc, 20.0)
+    x = np.tile([0.35, 0.65], (nc, 1))
+    Kp, S = oracle.line_params(mol, g, x)
+    sig = np.sqrt(g["sigma_turb"][0] ** 2 + KB * 20.0 / (mol["mass_amu"] * AMU))
+    phi = oracle.profile(g["n_ch"], g["v_min"], g["dv"], 0.0, sig)
+    nbg = planck_occ(mol["line_nu"][0], g["t_bg"])
+    tau1 = Kp[0, 0] * phi * g["h0"]
+    f = -np.expm1(-tau1) / tau1
+    for sign in (+1.0, -1.0):
+        g["dirs"] = np.array([[0.0, 0.0, sign]])
+        SIJ, ESC, NORM = oracle.march_grid3d(mol, g, Kp, S)
+        iz = np.arange(nc) // (N * N)
+        depth = iz if sign > 0 else (N - 1 - iz)
+        for c in range(nc):
+            Iin = nbg * np.exp(-depth[c] * tau1) - S[0, 0] * np.expm1(-depth[c] * tau1)
+            assert SIJ[0, c] / NORM[c] == pytest.approx((phi * Iin * f).sum() / phi.sum(), rel=1e-12)
+            assert ESC[0, c] / NORM[c] == pytest.approx((phi * f).sum() / phi.sum(), rel=1e-12)
+        np.testing.assert_allclose(NORM, phi.sum(), rtol=1e-13)
+
+
+def test_3d_isothermal_and_band_fraction(oracle):
+    """Moving 3D cloud at T_kin = T_bg: mean intensity n_bg everywhere; the
+    static version of the same grid gets NORM = band fraction in every cell
+    (every cell's weights add up to one over the 48 directions)."""
+    mol = LI.rotor_molecule(n_levels=5)
+    g = LI.small_grid3d(N=5, n_ch=24, nside=2)
+    nc = len(g["n_h2"])
+    g["t_kin"] = np.full(nc, g["t_bg"])
+    g["abundance"] = np.full(nc, 3e-3)
+    x = oracle.lte_populations(mol, g["t_kin"])
+    Kp, S = oracle.line_params(mol, g, x)
+    SIJ, ESC, NORM = oracle.march_grid3d(mol, g, Kp, S)
+    Jbar = (SIJ + S * (NORM - ESC)) / NORM
+    nbg = planck_occ(mol["line_nu"], g["t_bg"])[:, None]
+    np.testing.assert_allclose(Jbar, np.broadcast_to(nbg, Jbar.shape), rtol=1e-12)
+    for key in ("vx", "vy", "vz"):
+        g[key] = np.zeros(nc)
+    SIJ, ESC, NORM = oracle.march_grid3d(mol, g, Kp, S)
+    sig = np.sqrt(g["sigma_turb"][0] ** 2 + KB * g["t_kin"][0] / (mol["mass_amu"] * AMU))
+    phi = oracle.profile(g["n_ch"], g["v_min"], g["dv"], 0.0, sig)
+    np.testing.assert_allclose(NORM, phi.sum(), rtol=1e-13)
