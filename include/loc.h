@@ -1,0 +1,241 @@
+/*
+ * loc.h -- C ABI of the GB300 LOC line radiative-transfer library.
+ *
+ * The library runs the hot path of the accelerated lambda iteration (ALI)
+ * of Juvela's LOC (arXiv:2009.12609): for every ray and velocity channel a
+ * ray march across 1D shells or 3D cells evaluates the Doppler-shifted
+ * Gaussian profile, applies the formal solution I <- I e^-tau + S (1 - e^-tau)
+ * and accumulates each cell's absorbed-photon sum (SIJ) and escape term
+ * (ESC, the diagonal lambda operator), followed by a per-cell statistical-
+ * equilibrium solve (Sect. 2 of the paper, Eq. 1-3).  All steps run as
+ * CUDA kernels on one GPU (sm_103a); there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every function returns a loc_status; LOC_OK is 0, errors are negative.
+ *    loc_last_error() returns a thread-local message describing the last
+ *    error (valid until the next call on the same thread).
+ *  - All array arguments are HOST pointers unless stated otherwise.  The
+ *    library copies what it needs; the caller keeps ownership.  Outputs are
+ *    caller-allocated host buffers whose capacity n_out is checked first:
+ *    too small -> LOC_EINVAL and nothing is written.
+ *  - Units are CGS: cm, cm/s, cm^-3, K, Hz, s^-1, cm^3 s^-1.
+ *  - Handles are not thread-safe; use one handle per thread.
+ *  - Device memory comes from the allocator in loc_model_desc (or
+ *    cudaMalloc when it is NULL); work is queued on the given stream.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef LOC_H
+#define LOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int loc_status;
+#define LOC_OK        0
+#define LOC_EINVAL   -1   /* bad argument (size, range, NULL, layout)      */
+#define LOC_ENOMEM   -2   /* device or host allocation failed              */
+#define LOC_ECUDA    -3   /* a CUDA call failed (message has the details)  */
+#define LOC_ETIMEOUT -4   /* a bounded wait gave up                        */
+#define LOC_ENOTCONV -5   /* tolerance not reached within max_iter         */
+#define LOC_ESTATE   -6   /* call out of order (e.g. no molecule yet)      */
+#define LOC_EBUSY    -7   /* server has no free slot / memory              */
+
+/* Geometry kinds (Sect. 2.1 and 2.2). */
+#define LOC_SHELLS_1D 1
+#define LOC_GRID_3D   2
+#define LOC_OCTREE_3D 3
+
+/* Accumulation precision of the ray march. */
+#define LOC_FP32_MARCH 0  /* FP32 march and FP32 per-cell accumulators      */
+#define LOC_FP64_ACC   1  /* FP32 march, FP64 per-cell accumulators         */
+
+/* Optional device allocator; alloc returns NULL on failure. */
+typedef struct loc_allocator {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} loc_allocator;
+
+/*
+ * Model description (Sect. 2.1 for shells, Sect. 2.2 for 3D grids).
+ *  geometry     LOC_SHELLS_1D or LOC_GRID_3D (LOC_OCTREE_3D: see octree_*).
+ *  n_shells     1D: number of concentric shells K >= 1.
+ *  radius       1D: [K] outer radii, strictly increasing, > 0.
+ *  n_rays       1D: number of equidistant impact parameters
+ *               p_j = (j + 1/2) R / n_rays (0 -> n_shells).
+ *  n_root, h0   3D: N^3 root cells of size h0 (cm); cells are indexed
+ *               x fastest: idx = (iz N + iy) N + ix.
+ *  n_dir, dirs  3D: [n_dir][3] unit ray directions (e.g. HEALPix centres).
+ *  octree_levels, octree_refine, octree_n_cells
+ *               octree: number of levels below the root, and per cell a
+ *               refine flag (0 = leaf, 1 = split into 8 children) in level
+ *               order: level-0 cells in raster order, then the children of
+ *               every refined level-L cell, in the order of their parents,
+ *               each as the 8 octants (cx + 2 cy + 4 cz).  Per-cell field
+ *               arrays then follow this same order (values of refined
+ *               cells are ignored).
+ *  n_h2, t_kin, sigma_turb, abundance
+ *               per cell: H2 density, kinetic temperature, micro-turbulent
+ *               1D dispersion (cm/s), fractional abundance.
+ *  v            1D: [K] radial velocity (cm/s, > 0 outwards).
+ *  vx, vy, vz   3D: per-cell velocity (cm/s).
+ *  n_ch, v_min, dv  velocity channels: channel k covers
+ *               [v_min + k dv, v_min + (k+1) dv]; 1 <= n_ch <= 1024.
+ *  t_bg         background (CMB) temperature of the entering rays.
+ *  stream       cudaStream_t to queue all work on (NULL: legacy default).
+ *  allocator    optional device allocator (NULL: cudaMalloc / cudaFree).
+ */
+typedef struct loc_model_desc {
+    int geometry;
+    int n_shells;
+    const double *radius;
+    int n_rays;
+    int n_root;
+    double h0;
+    int n_dir;
+    const double *dirs;
+    int octree_levels;
+    const int32_t *octree_refine;
+    int64_t octree_n_cells;
+    const double *n_h2, *t_kin, *sigma_turb, *abundance;
+    const double *v;
+    const double *vx, *vy, *vz;
+    int n_ch;
+    double v_min, dv;
+    double t_bg;
+    void *stream;
+    const loc_allocator *allocator;
+} loc_model_desc;
+
+/*
+ * Molecule description.  Levels 0..n_levels-1 with energies E/k (K) and
+ * statistical weights; radiative lines u -> l with Einstein A and rest
+ * frequency; collisional pairs u > l with a constant downward rate
+ * coefficient k_ul (partner H2; upward rates follow from detailed balance).
+ * 2 <= n_levels <= 32.
+ */
+typedef struct loc_molecule_desc {
+    int n_levels;
+    const double *energy_K;
+    const double *g;
+    double mass_amu;
+    int n_lines;
+    const int32_t *line_u, *line_l;
+    const double *line_A, *line_nu;
+    int n_coll;
+    const int32_t *coll_u, *coll_l;
+    const double *coll_k;
+} loc_molecule_desc;
+
+/*
+ * Iteration options.
+ *  max_iter       number of ALI iterations to run (>= 1).
+ *  tol_tex        stop early once max |dT_ex|/|T_ex| < tol_tex (0: run
+ *                 exactly max_iter iterations).  The metric covers lines
+ *                 whose upper level holds >= 1e-6 of the molecules.
+ *  ali            1: accelerated lambda iteration with the diagonal
+ *                 operator (Sect. 2); 0: plain lambda iteration.
+ *  precision      LOC_FP32_MARCH or LOC_FP64_ACC.
+ *  lines_per_pass 0: all lines in one pass of the rays; k > 0: march the
+ *                 rays once per group of k lines (the paper's one-line-at-a-
+ *                 time mode is k = 1, Sect. 2).
+ *  window_sigmas  0: update every channel; w > 0: skip channels farther
+ *                 than w sigma from the local line centre (Sect. A.2).
+ */
+typedef struct loc_iter_opts {
+    int max_iter;
+    double tol_tex;
+    int ali;
+    int precision;
+    int lines_per_pass;
+    double window_sigmas;
+} loc_iter_opts;
+
+/* Iteration report. */
+typedef struct loc_iter_report {
+    int iterations;            /* iterations performed                      */
+    double max_rel_dtex;       /* metric of the last iteration              */
+    int64_t segments;          /* ray-cell steps per ray simulation         */
+    double updates;            /* (step, channel, line) updates, all iters  */
+    double kernel_ms;          /* device time of the iterations (events)    */
+    int64_t n_maser_cells;     /* (line, cell) pairs with negative opacity  */
+} loc_iter_report;
+
+typedef struct loc_model loc_model;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *loc_last_error(void);
+
+/* Library version string. */
+const char *loc_version(void);
+
+/* Build a model on the device (Sect. 2.1 / 2.2): validates and copies the
+ * description, precomputes the ray geometry.  *out receives the handle. */
+loc_status loc_create_model(loc_model **out, const loc_model_desc *d);
+
+/* Attach the molecule and reset the populations to LTE at T_kin (the
+ * iteration's starting point, Sect. 3.3.2).  May be called again. */
+loc_status loc_set_molecule(loc_model *m, const loc_molecule_desc *mol);
+
+/* Run ALI iterations (Sect. 2): per iteration, line parameters from the
+ * populations, one ray simulation accumulating SIJ / ESC / NORM, and the
+ * statistical-equilibrium solve.  r may be NULL.  Returns LOC_ENOTCONV
+ * (with the work done) if tol_tex > 0 was not reached in max_iter. */
+loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r);
+
+/* One ray simulation with the current populations, without the
+ * equilibrium solve: fills the per-cell accumulators read by
+ * loc_get_radiation (for step-by-step checks). */
+loc_status loc_march(loc_model *m, const loc_iter_opts *o);
+
+/* Per-cell accumulators of the last ray simulation, as FP64:
+ * sij, esc [n_lines][n_cells] and norm [n_cells] (any may be NULL).
+ * J_ext = SIJ / NORM and beta = ESC / NORM enter the rate equations. */
+loc_status loc_get_radiation(const loc_model *m, double *sij, double *esc,
+                             double *norm, size_t n_out_lines_cells,
+                             size_t n_out_cells);
+
+/* Level populations x[cell][level] (fractions summing to 1 per cell). */
+loc_status loc_get_populations(const loc_model *m, double *out, size_t n_out);
+
+/* Replace the populations (e.g. resume from a checkpoint); layout as above. */
+loc_status loc_set_populations(loc_model *m, const double *in, size_t n);
+
+/* Excitation temperatures of line t for all cells:
+ * T_ex = (h nu / k) / ln(g_u x_l / (g_l x_u)); 0 where a population is 0. */
+loc_status loc_get_tex(const loc_model *m, int t, double *out, size_t n_out);
+
+/* Emergent spectra of a 1D model (the final line-of-sight integration of
+ * Sect. 2): for each impact parameter p_cm[i] the ray is followed through
+ * the shells with the current populations; T_out[i][k] is the Rayleigh-
+ * Jeans brightness (h nu / k)(n_k - n_bg) of line t in channel k. */
+loc_status loc_spectra(const loc_model *m, int t, const double *p_cm, int n_p,
+                       double *T_out, size_t n_out);
+
+/* Number of cells (shells, grid cells or octree leaves+parents as given). */
+loc_status loc_model_info(const loc_model *m, int64_t *n_cells, int *n_levels,
+                          int *n_lines, int64_t *segments_per_sim);
+
+/* Segment list of one ray of a 3D model, traced on the device by the same
+ * walk the march uses: direction index dir, root line (i, j).  cells[k] is
+ * the cell index (x fastest for grids), dz[k] the main-axis length in
+ * fixed-point units (one root cell = 2^24).  *n_seg receives the count;
+ * LOC_EINVAL if it exceeds cap (nothing written). */
+loc_status loc_trace_ray(const loc_model *m, int dir, int64_t i, int64_t j,
+                         int64_t *cells, int64_t *dz, int64_t cap,
+                         int64_t *n_seg);
+
+/* Wait for all queued work of the model. */
+loc_status loc_sync(loc_model *m);
+
+/* Free the model and its device memory. */
+void loc_destroy(loc_model *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOC_H */

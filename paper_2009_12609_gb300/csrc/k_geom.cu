@@ -1,0 +1,210 @@
+// k_geom.cu -- ray geometry set-up kernels.
+//
+// 1D (Sect. 2.1): concentric shells with outer radii R_k, parallel rays with
+// equidistant impact parameters p_j = (j + 1/2) R / n_rays, each standing for
+// the annulus of area A_j = pi R^2 ((j+1)^2 - j^2) / n_rays^2.  A ray visits
+// shells K-1 .. t+1, its tangent shell t (smallest k with R_k > p) in two
+// halves, then t+1 .. K-1; step lengths are differences of
+// sqrt(R_k^2 - p^2).  The path lengths are precomputed once (the paper does
+// the same to speed up its kernel), in FP64, together with the line-of-sight
+// velocity at each step's start (Sect. 3.1: Doppler shift at the beginning of
+// the step; the outbound half of the tangent shell starts at cos = 0) and the
+// step's share of the cell's emission, w = A_j s / W_c with
+// W_c = sum over steps in c of A_j s (Sect. 2: sum(s) is known).
+//
+// 3D (Sect. 2.2): per direction the main axis, the mirrored axes and the
+// fixed-point slopes of the ray lattice (see walk3d.cuh).
+#include "loc_internal.cuh"
+#include "walk3d.cuh"
+
+namespace loc {
+
+__device__ __forceinline__ double ray_p(const DevModel &m, int j)
+{
+    return (j + 0.5) * m.radius[m.K - 1] / m.n_rays;
+}
+
+__device__ __forceinline__ double ray_area(const DevModel &m, int j)
+{
+    const double R = m.radius[m.K - 1];
+    return kPI * R * R * ((j + 1.0) * (j + 1.0) - (double)j * j) / ((double)m.n_rays * m.n_rays);
+}
+
+__device__ __forceinline__ int tangent_shell(const DevModel &m, double p)
+{
+    int lo = 0, hi = m.K;            // first k with R_k > p (binary search)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (m.radius[mid] > p) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// segment lengths of ray p through shell k (k > t): both crossings equal
+__device__ __forceinline__ double shell_chord(const DevModel &m, int k, double p)
+{
+    const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+    const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
+    return zo - zi;
+}
+
+// one thread: tangent shells, per-ray step counts and offsets (prefix sum)
+__global__ void geom1d_offsets(DevModel m, int *tan)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int off = 0;
+    for (int j = 0; j < m.n_rays; j++) {
+        const int t = tangent_shell(m, ray_p(m, j));
+        tan[j] = t;
+        m.ray_off[j] = off;
+        off += (t < m.K) ? 2 * (m.K - t) : 0;
+    }
+    m.ray_off[m.n_rays] = off;
+}
+
+// thread per shell: W_k = sum_j A_j (length of ray j inside shell k)
+__global__ void geom1d_weights(DevModel m, const int *tan, double *W)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m.K) return;
+    double acc = 0.0;
+    for (int j = 0; j < m.n_rays; j++) {
+        const int t = tan[j];
+        if (t > k) continue;
+        const double p = ray_p(m, j);
+        const double s = (t == k) ? sqrt(m.radius[k] * m.radius[k] - p * p) : shell_chord(m, k, p);
+        acc += ray_area(m, j) * 2.0 * s;     // two steps per shell
+    }
+    W[k] = acc;
+}
+
+// thread per ray: fill the step records
+__global__ void geom1d_fill(DevModel m, const int *tan, const double *W)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.n_rays) return;
+    const int t = tan[j];
+    if (t >= m.K) return;
+    const double p = ray_p(m, j);
+    const double A = ray_area(m, j);
+    Seg1D *out = m.segs + m.ray_off[j];
+    int n = 0;
+    auto put = [&](int k, double s, double cosv) {
+        Seg1D sg;
+        sg.cell = k;
+        sg.s = (float)s;
+        sg.vlos = (float)((double)m.v1d[k] * cosv);
+        sg.w = (float)((W[k] > 0.0) ? A * s / W[k] : 0.0);
+        out[n++] = sg;
+    };
+    for (int k = m.K - 1; k > t; k--) {
+        const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+        const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
+        put(k, zo - zi, -zo / m.radius[k]);
+    }
+    const double zt = sqrt(m.radius[t] * m.radius[t] - p * p);
+    put(t, zt, -zt / m.radius[t]);
+    put(t, zt, 0.0);
+    for (int k = t + 1; k < m.K; k++) {
+        const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+        const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
+        put(k, zo - zi, zi / m.radius[k - 1]);
+    }
+}
+
+loc_status launch_geom1d(const DevModel &m, cudaStream_t st)
+{
+    int *tan = nullptr;
+    double *W = nullptr;
+    LOC_CUDA_TRY(cudaMallocAsync(&tan, sizeof(int) * m.n_rays, st));
+    LOC_CUDA_TRY(cudaMallocAsync(&W, sizeof(double) * m.K, st));
+    geom1d_offsets<<<1, 1, 0, st>>>(m, tan);
+    geom1d_weights<<<(m.K + 127) / 128, 128, 0, st>>>(m, tan, W);
+    geom1d_fill<<<(m.n_rays + 127) / 128, 128, 0, st>>>(m, tan, W);
+    LOC_CUDA_TRY(cudaGetLastError());
+    LOC_CUDA_TRY(cudaFreeAsync(tan, st));
+    LOC_CUDA_TRY(cudaFreeAsync(W, st));
+    return LOC_OK;
+}
+
+// ----------------------------------------------------------------------------
+// 3D: trace one root line and record its segments (tests / diagnostics)
+// ----------------------------------------------------------------------------
+__global__ void trace3d_kernel(DevModel m, int dir, long long i, long long j,
+                               long long *cells, long long *dz, long long cap,
+                               long long *n_out)
+{
+    if (threadIdx.x != 0) return;
+    const Dir3D D = m.dirs[dir];
+    long long n = 0;
+    walk_grid3d(D, m.N, i, j, [&](long long c, long long d) {
+        if (n < cap) { cells[n] = c; dz[n] = d; }
+        n++;
+    });
+    *n_out = n;
+}
+
+loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,
+                          long long *cells, long long *dz, long long cap,
+                          long long *n_out, cudaStream_t st)
+{
+    trace3d_kernel<<<1, 32, 0, st>>>(m, dir, i, j, cells, dz, cap, n_out);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+
+// ----------------------------------------------------------------------------
+// 3D direction decomposition (FP64, same arithmetic as the lattice definition)
+// ----------------------------------------------------------------------------
+__global__ void dir_setup_kernel(const double *dirs, int n_dir, double h0, Dir3D *out)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_dir) return;
+    const double d[3] = {dirs[3 * id], dirs[3 * id + 1], dirs[3 * id + 2]};
+    int mm = 0;
+    if (fabs(d[1]) > fabs(d[mm])) mm = 1;
+    if (fabs(d[2]) > fabs(d[mm])) mm = 2;
+    Dir3D D;
+    D.m = mm;
+    D.a = (mm == 0) ? 1 : 0;
+    D.b = (mm == 2) ? 1 : 2;
+    const double scale = ldexp(1.0, kFixedBits);
+    for (int k = 0; k < 3; k++) { D.flip[k] = d[k] < 0.0; D.d[k] = (float)d[k]; }
+    D.qa = (long long)floor(scale * fabs(d[D.a]) / fabs(d[mm]) + 0.5);
+    D.qb = (long long)floor(scale * fabs(d[D.b]) / fabs(d[mm]) + 0.5);
+    D.unit = (float)(h0 / scale / fabs(d[mm]));
+    out[id] = D;
+}
+
+loc_status launch_dir_setup(const double *dirs_dev, int n_dir, double h0, Dir3D *out,
+                            cudaStream_t st)
+{
+    dir_setup_kernel<<<(n_dir + 63) / 64, 64, 0, st>>>(dirs_dev, n_dir, h0, out);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+// per cell: 1 / (sqrt(2) sigma) with sigma^2 = sigma_turb^2 + k T / m, and the
+// packed 3D record {vx, vy, vz, 1/(sqrt(2) sigma)}
+__global__ void cell_setup_kernel(DevModel m, const double *sigma_turb, const double *vx,
+                                  const double *vy, const double *vz)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.n_cells) return;
+    const double sig = sqrt(sigma_turb[c] * sigma_turb[c] + kKB * m.t_kin[c] / (m.mass_amu * kAMU));
+    const float inv = (float)(1.0 / (sqrt(2.0) * sig));
+    m.inv_s2sig[c] = inv;
+    if (m.vel) m.vel[c] = make_float4((float)vx[c], (float)vy[c], (float)vz[c], inv);
+}
+
+loc_status launch_cell_setup(const DevModel &m, const double *sigma_turb, const double *vx,
+                             const double *vy, const double *vz, cudaStream_t st)
+{
+    const long long nb = (m.n_cells + 255) / 256;
+    cell_setup_kernel<<<(unsigned)nb, 256, 0, st>>>(m, sigma_turb, vx, vy, vz);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+}  // namespace loc

@@ -1,0 +1,244 @@
+// k_se.cu -- level populations: LTE start, background, line parameters,
+// statistical-equilibrium solve and excitation temperatures.
+//
+// Line parameters (Eq. 2, Eq. 3): the optical depth of a step of length s in
+// channel k is tau = K phi_k s with
+//   K = c^3 A / (8 pi nu^3 dv) n_mol (x_l g_u / g_l - x_u)
+// and the source function in occupation units is
+//   S = g_l x_u / (g_u x_l - g_l x_u).
+// A vanishing population difference (|g_u x_l - g_l x_u| <= 1e-30 g_u x_l)
+// gives K = 0, S = 0; inverted populations (K < 0) are kept and counted.
+//
+// Statistical equilibrium (Sect. 2, ALI paragraph): the radiative rates use
+// the cell averages J_ext = SIJ / NORM and beta = ESC / NORM in place of
+// B_lu I_nu; with ALI the locally absorbed photons are removed from J and
+// A_ul is scaled by beta:
+//   R_lu = (g_u / g_l) A J_ext,   R_ul = A (beta + J_ext);
+// without ALI J = J_ext + S (1 - beta) and beta = 1.  Collisions with H2:
+// C_ul = n_H2 k_ul, C_lu = C_ul (g_u / g_l) exp(-(E_u - E_l) / T_kin).  The
+// first balance equation is replaced by sum(x) = 1 and the system is solved
+// in FP64 by Gaussian elimination with partial pivoting, one cell per
+// thread.  The same kernel reports max |dT_ex| / |T_ex| over cells and lines
+// whose upper level holds at least 1e-6 of the molecules.
+#include "loc_internal.cuh"
+
+namespace loc {
+
+__global__ void lte_kernel(DevModel m)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.n_cells) return;
+    double z = 0.0;
+    double *x = m.x + c * m.L;
+    for (int i = 0; i < m.L; i++) {
+        x[i] = m.g[i] * exp(-m.energy_K[i] / m.t_kin[c]);
+        z += x[i];
+    }
+    for (int i = 0; i < m.L; i++) x[i] /= z;
+}
+
+loc_status launch_lte(const DevModel &m, cudaStream_t st)
+{
+    lte_kernel<<<(unsigned)((m.n_cells + 255) / 256), 256, 0, st>>>(m);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+// background occupation n_bg = 1 / (exp(h nu / k T_bg) - 1) per line (Eq. 1:
+// rays enter carrying the background field)
+__global__ void bg_kernel(DevModel m)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const double n = (m.t_bg > 0.0) ? 1.0 / expm1(kH * m.line_nu[t] / (kKB * m.t_bg)) : 0.0;
+    m.nbg64[t] = n;
+    m.nbg[t] = (float)n;
+}
+
+loc_status launch_bg(const DevModel &m, cudaStream_t st)
+{
+    bg_kernel<<<(m.T + 63) / 64, 64, 0, st>>>(m);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+__global__ void line_params_kernel(DevModel m)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m.T * m.n_cells) return;
+    const int t = (int)(idx / m.n_cells);
+    const long long c = idx - (long long)t * m.n_cells;
+    const int u = m.line_u[t], l = m.line_l[t];
+    const double nu = m.line_nu[t];
+    const double gu = m.g[u], gl = m.g[l];
+    const double xl = m.x[c * m.L + l], xu = m.x[c * m.L + u];
+    const double diff = gu * xl - gl * xu;
+    float2 ks;
+    if (fabs(diff) <= 1e-30 * gu * xl || (xl == 0.0 && xu == 0.0)) {
+        ks = make_float2(0.f, 0.f);
+    } else {
+        const double pre = kC * kC * kC * m.line_A[t] / (8.0 * kPI * nu * nu * nu * m.dv);
+        const double K = pre * m.n_h2[c] * m.abundance[c] * diff / gl;
+        ks = make_float2((float)K, (float)(gl * xu / diff));
+        if (K < 0.0) atomicAdd(m.maser_count, 1ull);
+    }
+    m.ks[idx] = ks;
+}
+
+loc_status launch_line_params(const DevModel &m, cudaStream_t st)
+{
+    const long long n = (long long)m.T * m.n_cells;
+    line_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+__device__ __forceinline__ double tex_of(const DevModel &m, int t, const double *x)
+{
+    const int u = m.line_u[t], l = m.line_l[t];
+    const double xu = x[u], xl = x[l];
+    if (!(xu > 0.0) || !(xl > 0.0)) return 0.0;
+    return (kH * m.line_nu[t] / kKB) / log(m.g[u] * xl / (m.g[l] * xu));
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(128) se_kernel(DevModel m, int ali, int fp64_acc)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float my_d = 0.f;
+    if (c < m.n_cells) {
+        const int L = m.L;
+        double M[LMAX][LMAX + 1];
+        for (int i = 0; i < L; i++)
+            for (int j = 0; j <= L; j++) M[i][j] = 0.0;
+        // norm
+        double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
+        for (int t = 0; t < m.T; t++) {
+            const int u = m.line_u[t], l = m.line_l[t];
+            const double A = m.line_A[t];
+            const long long o = (long long)t * m.n_cells + c;
+            double J, beta;
+            if (nrm > 0.0) {
+                double s, e;
+                if (fp64_acc) { s = m.acc64[2 * o]; e = m.acc64[2 * o + 1]; }
+                else { const float2 a = m.acc[o]; s = a.x; e = a.y; }
+                J = s / nrm;
+                beta = e / nrm;
+            } else {
+                J = m.nbg64[t];
+                beta = 1.0;
+            }
+            if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
+            const double rul = A * (beta + J);
+            const double rlu = (m.g[u] / m.g[l]) * A * J;
+            M[l][u] += rul; M[u][u] -= rul;
+            M[u][l] += rlu; M[l][l] -= rlu;
+        }
+        const double T = m.t_kin[c], nh = m.n_h2[c];
+        for (int p = 0; p < m.P; p++) {
+            const int u = m.coll_u[p], l = m.coll_l[p];
+            const double cul = nh * m.coll_k[p];
+            const double clu = cul * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / T);
+            M[l][u] += cul; M[u][u] -= cul;
+            M[u][l] += clu; M[l][l] -= clu;
+        }
+        for (int j = 0; j < L; j++) M[0][j] = 1.0;
+        M[0][L] = 1.0;
+        // Gaussian elimination with partial pivoting (augmented column L)
+        for (int p = 0; p < L; p++) {
+            int piv = p;
+            double best = fabs(M[p][p]);
+            for (int i = p + 1; i < L; i++)
+                if (fabs(M[i][p]) > best) { best = fabs(M[i][p]); piv = i; }
+            if (piv != p)
+                for (int j = p; j <= L; j++) { const double tmp = M[p][j]; M[p][j] = M[piv][j]; M[piv][j] = tmp; }
+            const double inv = 1.0 / M[p][p];
+            for (int i = p + 1; i < L; i++) {
+                const double f = M[i][p] * inv;
+                if (f == 0.0) continue;
+                for (int j = p; j <= L; j++) M[i][j] -= f * M[p][j];
+            }
+        }
+        double xs[LMAX];
+        for (int i = L - 1; i >= 0; i--) {
+            double a = M[i][L];
+            for (int j = i + 1; j < L; j++) a -= M[i][j] * xs[j];
+            xs[i] = a / M[i][i];
+        }
+        double *xo = m.x + c * L;
+        double *xn = m.x_new + c * L;
+        for (int i = 0; i < L; i++) xn[i] = xs[i];
+        for (int t = 0; t < m.T; t++) {
+            if (xs[m.line_u[t]] < 1e-6) continue;
+            const double a = tex_of(m, t, xo);
+            if (a == 0.0) continue;
+            const double b = tex_of(m, t, xs);
+            const float d = (float)(fabs(b - a) / fabs(a));
+            my_d = fmaxf(my_d, d);
+        }
+    }
+    // block max -> one atomic (non-negative floats order like their bits)
+    for (int off = 16; off > 0; off >>= 1) my_d = fmaxf(my_d, __shfl_xor_sync(0xffffffffu, my_d, off));
+    __shared__ float wmax[4];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = my_d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v = fmaxf(v, wmax[w]);
+        if (v > 0.f) atomicMax(m.dtex_bits, __float_as_uint(v));
+    }
+}
+
+loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((m.n_cells + 127) / 128);
+    if (m.L <= 4) se_kernel<4><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
+    else if (m.L <= 8) se_kernel<8><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
+    else if (m.L <= 16) se_kernel<16><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
+    else se_kernel<32><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+__global__ void tex_kernel(DevModel m, int t, double *out)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.n_cells) return;
+    out[c] = tex_of(m, t, m.x + c * m.L);
+}
+
+loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st)
+{
+    tex_kernel<<<(unsigned)((m.n_cells + 255) / 256), 256, 0, st>>>(m, t, out_dev);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+// accumulators -> FP64 arrays (diagnostics)
+__global__ void acc_to_f64_kernel(DevModel m, int fp64_acc, double *sij, double *esc, double *norm)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)m.T * m.n_cells;
+    if (idx < n) {
+        if (fp64_acc) {
+            if (sij) sij[idx] = m.acc64[2 * idx];
+            if (esc) esc[idx] = m.acc64[2 * idx + 1];
+        } else {
+            const float2 a = m.acc[idx];
+            if (sij) sij[idx] = a.x;
+            if (esc) esc[idx] = a.y;
+        }
+    }
+    if (idx < m.n_cells && norm) norm[idx] = fp64_acc ? m.norm64[idx] : (double)m.norm[idx];
+}
+
+loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,
+                             double *norm, cudaStream_t st)
+{
+    const long long n = (long long)m.T * m.n_cells;
+    acc_to_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, fp64_acc, sij, esc, norm);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+}  // namespace loc

@@ -1,0 +1,576 @@
+// loc_api.cu -- the C ABI (include/loc.h): model and molecule set-up, the
+// ALI iteration loop, result getters.  Argument marshalling, validation and
+// launch sequencing only; every step of the method runs in the kernels of
+// k_geom.cu, k_march.cu and k_se.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "loc_internal.cuh"
+
+namespace loc {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace loc
+
+using namespace loc;
+
+struct loc_model {
+    DevModel d;
+    cudaStream_t st = nullptr;
+    loc_allocator alloc{};
+    bool custom_alloc = false;
+    std::vector<void *> geo_mem;     // lives as long as the model
+    std::vector<void *> mol_mem;     // replaced by loc_set_molecule
+    double *sigma_turb = nullptr;    // device copies kept for set_molecule
+    double *vx = nullptr, *vy = nullptr, *vz = nullptr;
+    bool has_mol = false;
+    bool has_rad = false;
+    int last_fp64 = 0;
+    long long segs_per_sim = 0;
+};
+
+static void *dev_alloc(loc_model *m, size_t bytes, std::vector<void *> &owner)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (m->custom_alloc) {
+        p = m->alloc.alloc(bytes, m->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) owner.push_back(p);
+    return p;
+}
+
+static void dev_free_all(loc_model *m, std::vector<void *> &owner)
+{
+    for (void *p : owner) {
+        if (m->custom_alloc) m->alloc.free(p, m->alloc.ctx);
+        else cudaFree(p);
+    }
+    owner.clear();
+}
+
+template <class T>
+static loc_status upload(loc_model *m, T **dst, const T *src, size_t n, std::vector<void *> &owner,
+                         const char *what)
+{
+    *dst = (T *)dev_alloc(m, sizeof(T) * n, owner);
+    if (!*dst) {
+        set_error("device allocation of %s (%zu bytes) failed", what, sizeof(T) * n);
+        return LOC_ENOMEM;
+    }
+    if (src) LOC_CUDA_TRY(cudaMemcpyAsync(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, m->st));
+    return LOC_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        loc_status _s = (x);            \
+        if (_s != LOC_OK) return _s;    \
+    } while (0)
+
+#define CHECK(cond, ...)                \
+    do {                                \
+        if (!(cond)) {                  \
+            set_error(__VA_ARGS__);     \
+            return LOC_EINVAL;          \
+        }                               \
+    } while (0)
+
+static bool finite_pos(const double *a, long long n, bool allow_zero)
+{
+    for (long long i = 0; i < n; i++) {
+        if (!std::isfinite(a[i])) return false;
+        if (allow_zero ? a[i] < 0.0 : a[i] <= 0.0) return false;
+    }
+    return true;
+}
+
+static bool finite_all(const double *a, long long n)
+{
+    for (long long i = 0; i < n; i++)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+extern "C" {
+
+const char *loc_last_error(void) { return g_err; }
+
+const char *loc_version(void) { return "loc-gb300 0.1 (sm_103a)"; }
+
+static loc_status create_impl(loc_model *m, const loc_model_desc *d)
+{
+    DevModel &D = m->d;
+    memset(&D, 0, sizeof(D));
+    D.geometry = d->geometry;
+    D.n_ch = d->n_ch;
+    D.v_min = d->v_min;
+    D.dv = d->dv;
+    D.t_bg = d->t_bg;
+    CHECK(d->n_ch >= 1 && d->n_ch <= kMaxChannels, "n_ch must be in [1, %d], got %d", kMaxChannels, d->n_ch);
+    CHECK(std::isfinite(d->v_min) && d->dv > 0.0 && std::isfinite(d->dv), "channel grid: need finite v_min and dv > 0");
+    CHECK(std::isfinite(d->t_bg) && d->t_bg >= 0.0, "t_bg must be >= 0");
+    long long nc = 0;
+    if (d->geometry == LOC_SHELLS_1D) {
+        CHECK(d->n_shells >= 1 && d->n_shells <= (1 << 16), "n_shells must be in [1, 65536]");
+        CHECK(d->radius && d->v, "1D model needs radius and v");
+        const int K = d->n_shells;
+        CHECK(finite_pos(d->radius, K, false), "radius must be finite and > 0");
+        for (int k = 1; k < K; k++) CHECK(d->radius[k] > d->radius[k - 1], "radius must increase strictly");
+        CHECK(finite_all(d->v, K), "v must be finite");
+        nc = K;
+        D.K = K;
+        D.n_rays = d->n_rays > 0 ? d->n_rays : K;
+        CHECK(D.n_rays <= (1 << 16), "n_rays must be <= 65536");
+    } else if (d->geometry == LOC_GRID_3D) {
+        CHECK(d->n_root >= 1 && d->n_root <= 1024, "n_root must be in [1, 1024]");
+        CHECK(d->h0 > 0.0 && std::isfinite(d->h0), "h0 must be > 0");
+        CHECK(d->n_dir >= 1 && d->dirs, "3D model needs directions");
+        for (int i = 0; i < d->n_dir; i++) {
+            const double *v = d->dirs + 3 * i;
+            const double n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            CHECK(std::isfinite(n2) && fabs(n2 - 1.0) < 1e-6, "direction %d is not a unit vector", i);
+        }
+        CHECK(d->vx && d->vy && d->vz, "3D model needs vx, vy, vz");
+        nc = (long long)d->n_root * d->n_root * d->n_root;
+        D.N = d->n_root;
+        D.n_dir = d->n_dir;
+        D.h0 = d->h0;
+    } else if (d->geometry == LOC_OCTREE_3D) {
+        set_error("octree models are not available in this build");
+        return LOC_EINVAL;
+    } else {
+        CHECK(false, "unknown geometry %d", d->geometry);
+    }
+    D.n_cells = nc;
+    CHECK(d->n_h2 && d->t_kin && d->sigma_turb && d->abundance, "per-cell arrays missing");
+    CHECK(finite_pos(d->n_h2, nc, true), "n_h2 must be finite and >= 0");
+    CHECK(finite_pos(d->t_kin, nc, false), "t_kin must be finite and > 0");
+    CHECK(finite_pos(d->sigma_turb, nc, true), "sigma_turb must be finite and >= 0");
+    CHECK(finite_pos(d->abundance, nc, true), "abundance must be finite and >= 0");
+
+    TRY(upload(m, &D.n_h2, d->n_h2, nc, m->geo_mem, "n_h2"));
+    TRY(upload(m, &D.t_kin, d->t_kin, nc, m->geo_mem, "t_kin"));
+    TRY(upload(m, &D.abundance, d->abundance, nc, m->geo_mem, "abundance"));
+    TRY(upload(m, &m->sigma_turb, d->sigma_turb, nc, m->geo_mem, "sigma_turb"));
+    TRY(upload<float>(m, &D.inv_s2sig, nullptr, nc, m->geo_mem, "inv_s2sig"));
+
+    if (d->geometry == LOC_SHELLS_1D) {
+        const int K = D.K;
+        TRY(upload(m, &D.radius, d->radius, K, m->geo_mem, "radius"));
+        std::vector<float> v1(K);
+        for (int k = 0; k < K; k++) v1[k] = (float)d->v[k];
+        TRY(upload(m, &D.v1d, v1.data(), K, m->geo_mem, "v"));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));     // v1 leaves scope
+        TRY(upload<int>(m, &D.ray_off, nullptr, D.n_rays + 1, m->geo_mem, "ray offsets"));
+        const long long cap = 2ll * D.n_rays * (K + 1);
+        TRY(upload<Seg1D>(m, &D.segs, nullptr, cap, m->geo_mem, "ray steps"));
+        TRY(launch_geom1d(D, m->st));
+        int total = 0;
+        LOC_CUDA_TRY(cudaMemcpyAsync(&total, D.ray_off + D.n_rays, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        D.n_segs = total;
+        m->segs_per_sim = total;
+    } else {
+        TRY(upload(m, &m->vx, d->vx, nc, m->geo_mem, "vx"));
+        TRY(upload(m, &m->vy, d->vy, nc, m->geo_mem, "vy"));
+        TRY(upload(m, &m->vz, d->vz, nc, m->geo_mem, "vz"));
+        TRY(upload<float4>(m, &D.vel, nullptr, nc, m->geo_mem, "velocity records"));
+        double *dirs = nullptr;
+        TRY(upload(m, &dirs, d->dirs, 3 * (size_t)d->n_dir, m->geo_mem, "dirs"));
+        TRY(upload<Dir3D>(m, &D.dirs, nullptr, d->n_dir, m->geo_mem, "direction records"));
+        TRY(launch_dir_setup(dirs, d->n_dir, d->h0, D.dirs, m->st));
+        m->segs_per_sim = -1;    // counted on demand
+    }
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    return LOC_OK;
+}
+
+loc_status loc_create_model(loc_model **out, const loc_model_desc *d)
+{
+    if (!out || !d) { set_error("NULL argument"); return LOC_EINVAL; }
+    *out = nullptr;
+    loc_model *m = new (std::nothrow) loc_model();
+    if (!m) { set_error("host allocation failed"); return LOC_ENOMEM; }
+    m->st = (cudaStream_t)d->stream;
+    if (d->allocator) {
+        if (!d->allocator->alloc || !d->allocator->free) {
+            delete m;
+            set_error("allocator needs alloc and free");
+            return LOC_EINVAL;
+        }
+        m->alloc = *d->allocator;
+        m->custom_alloc = true;
+    }
+    loc_status s = create_impl(m, d);
+    if (s != LOC_OK) {
+        cudaStreamSynchronize(m->st);
+        dev_free_all(m, m->geo_mem);
+        delete m;
+        return s;
+    }
+    *out = m;
+    return LOC_OK;
+}
+
+static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
+{
+    DevModel &D = m->d;
+    CHECK(mol->n_levels >= 2 && mol->n_levels <= kMaxLevels, "n_levels must be in [2, %d]", kMaxLevels);
+    CHECK(mol->n_lines >= 1 && mol->n_lines <= kMaxLines, "n_lines must be in [1, %d]", kMaxLines);
+    CHECK(mol->n_coll >= 0, "n_coll must be >= 0");
+    CHECK(mol->energy_K && mol->g && mol->line_u && mol->line_l && mol->line_A && mol->line_nu,
+          "molecule arrays missing");
+    CHECK(mol->n_coll == 0 || (mol->coll_u && mol->coll_l && mol->coll_k), "collision arrays missing");
+    CHECK(mol->mass_amu > 0.0 && std::isfinite(mol->mass_amu), "mass_amu must be > 0");
+    const int L = mol->n_levels;
+    CHECK(finite_pos(mol->g, L, false), "g must be > 0");
+    CHECK(finite_all(mol->energy_K, L), "energies must be finite");
+    for (int t = 0; t < mol->n_lines; t++) {
+        const int u = mol->line_u[t], l = mol->line_l[t];
+        CHECK(u >= 0 && u < L && l >= 0 && l < L && u != l, "line %d: bad levels", t);
+        CHECK(mol->line_A[t] >= 0.0 && mol->line_nu[t] > 0.0, "line %d: bad A or nu", t);
+    }
+    for (int p = 0; p < mol->n_coll; p++) {
+        const int u = mol->coll_u[p], l = mol->coll_l[p];
+        CHECK(u >= 0 && u < L && l >= 0 && l < L && u != l, "collision %d: bad levels", p);
+        CHECK(mol->coll_k[p] >= 0.0 && std::isfinite(mol->coll_k[p]), "collision %d: bad rate", p);
+    }
+    D.L = L;
+    D.T = mol->n_lines;
+    D.P = mol->n_coll;
+    D.mass_amu = mol->mass_amu;
+    std::vector<int> lu(mol->line_u, mol->line_u + D.T), ll(mol->line_l, mol->line_l + D.T);
+    std::vector<int> cu(mol->coll_u, mol->coll_u + D.P), cl(mol->coll_l, mol->coll_l + D.P);
+    TRY(upload(m, &D.energy_K, mol->energy_K, L, m->mol_mem, "energies"));
+    TRY(upload(m, &D.g, mol->g, L, m->mol_mem, "weights"));
+    TRY(upload(m, &D.line_u, lu.data(), D.T, m->mol_mem, "line_u"));
+    TRY(upload(m, &D.line_l, ll.data(), D.T, m->mol_mem, "line_l"));
+    TRY(upload(m, &D.line_A, mol->line_A, D.T, m->mol_mem, "line_A"));
+    TRY(upload(m, &D.line_nu, mol->line_nu, D.T, m->mol_mem, "line_nu"));
+    TRY(upload(m, &D.coll_u, cu.data(), D.P, m->mol_mem, "coll_u"));
+    TRY(upload(m, &D.coll_l, cl.data(), D.P, m->mol_mem, "coll_l"));
+    TRY(upload(m, &D.coll_k, mol->coll_k, D.P, m->mol_mem, "coll_k"));
+    const long long nc = D.n_cells;
+    TRY(upload<float>(m, &D.nbg, nullptr, D.T, m->mol_mem, "nbg"));
+    TRY(upload<double>(m, &D.nbg64, nullptr, D.T, m->mol_mem, "nbg64"));
+    TRY(upload<double>(m, &D.x, nullptr, nc * L, m->mol_mem, "populations"));
+    TRY(upload<double>(m, &D.x_new, nullptr, nc * L, m->mol_mem, "populations"));
+    TRY(upload<float2>(m, &D.ks, nullptr, nc * D.T, m->mol_mem, "line parameters"));
+    TRY(upload<float2>(m, &D.acc, nullptr, nc * D.T, m->mol_mem, "accumulators"));
+    TRY(upload<float>(m, &D.norm, nullptr, nc, m->mol_mem, "norm"));
+    TRY(upload<double>(m, &D.acc64, nullptr, 2 * nc * D.T, m->mol_mem, "accumulators64"));
+    TRY(upload<double>(m, &D.norm64, nullptr, nc, m->mol_mem, "norm64"));
+    TRY(upload<unsigned int>(m, &D.dtex_bits, nullptr, 1, m->mol_mem, "dtex"));
+    TRY(upload<unsigned long long>(m, &D.maser_count, nullptr, 1, m->mol_mem, "maser count"));
+    TRY(launch_cell_setup(D, m->sigma_turb, m->vx, m->vy, m->vz, m->st));
+    TRY(launch_bg(D, m->st));
+    TRY(launch_lte(D, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));    // host vectors leave scope
+    return LOC_OK;
+}
+
+loc_status loc_set_molecule(loc_model *m, const loc_molecule_desc *mol)
+{
+    if (!m || !mol) { set_error("NULL argument"); return LOC_EINVAL; }
+    cudaStreamSynchronize(m->st);
+    dev_free_all(m, m->mol_mem);
+    m->has_mol = false;
+    m->has_rad = false;
+    loc_status s = set_molecule_impl(m, mol);
+    if (s != LOC_OK) {
+        cudaStreamSynchronize(m->st);
+        dev_free_all(m, m->mol_mem);
+        return s;
+    }
+    m->has_mol = true;
+    return LOC_OK;
+}
+
+static loc_status check_opts(const loc_iter_opts *o)
+{
+    CHECK(o, "NULL options");
+    CHECK(o->max_iter >= 1, "max_iter must be >= 1");
+    CHECK(o->tol_tex >= 0.0 && std::isfinite(o->tol_tex), "tol_tex must be >= 0");
+    CHECK(o->precision == LOC_FP32_MARCH || o->precision == LOC_FP64_ACC, "unknown precision");
+    CHECK(o->lines_per_pass >= 0, "lines_per_pass must be >= 0");
+    CHECK(o->window_sigmas >= 0.0 && std::isfinite(o->window_sigmas), "window_sigmas must be >= 0");
+    return LOC_OK;
+}
+
+// one ray simulation: zero the accumulators, then one march per line group
+static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
+{
+    DevModel &D = m->d;
+    const int fp64 = o->precision == LOC_FP64_ACC;
+    if (fp64) {
+        LOC_CUDA_TRY(cudaMemsetAsync(D.acc64, 0, sizeof(double) * 2 * D.T * D.n_cells, m->st));
+        LOC_CUDA_TRY(cudaMemsetAsync(D.norm64, 0, sizeof(double) * D.n_cells, m->st));
+    } else {
+        LOC_CUDA_TRY(cudaMemsetAsync(D.acc, 0, sizeof(float2) * D.T * D.n_cells, m->st));
+        LOC_CUDA_TRY(cudaMemsetAsync(D.norm, 0, sizeof(float) * D.n_cells, m->st));
+    }
+    int per = o->lines_per_pass > 0 ? o->lines_per_pass : D.T;
+    if (per > kMaxLinesPerWarp) per = kMaxLinesPerWarp;
+    for (int l0 = 0; l0 < D.T; l0 += per) {
+        MarchArgs a;
+        a.line0 = l0;
+        a.n_lines = (D.T - l0 < per) ? D.T - l0 : per;
+        a.window = (float)o->window_sigmas;
+        a.fp64_acc = fp64;
+        a.do_norm = (l0 == 0);
+        TRY(launch_march(D, a, m->st));
+    }
+    m->has_rad = true;
+    m->last_fp64 = fp64;
+    return LOC_OK;
+}
+
+loc_status loc_march(loc_model *m, const loc_iter_opts *o)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    TRY(check_opts(o));
+    if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
+    TRY(launch_line_params(m->d, m->st));
+    TRY(march_impl(m, o));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    return LOC_OK;
+}
+
+loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    TRY(check_opts(o));
+    if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
+    DevModel &D = m->d;
+    cudaEvent_t e0, e1;
+    LOC_CUDA_TRY(cudaEventCreate(&e0));
+    LOC_CUDA_TRY(cudaEventCreate(&e1));
+    LOC_CUDA_TRY(cudaMemsetAsync(D.maser_count, 0, sizeof(unsigned long long), m->st));
+    LOC_CUDA_TRY(cudaEventRecord(e0, m->st));
+    int it = 0;
+    float dtex = 0.f;
+    bool converged = false;
+    loc_status st = LOC_OK;
+    for (it = 0; it < o->max_iter; it++) {
+        if ((st = launch_line_params(D, m->st)) != LOC_OK) break;
+        if ((st = march_impl(m, o)) != LOC_OK) break;
+        if (cudaMemsetAsync(D.dtex_bits, 0, sizeof(unsigned), m->st) != cudaSuccess) { st = LOC_ECUDA; break; }
+        if ((st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st)) != LOC_OK) break;
+        std::swap(D.x, D.x_new);
+        if (o->tol_tex > 0.0 || it == o->max_iter - 1) {
+            unsigned bits = 0;
+            if (cudaMemcpyAsync(&bits, D.dtex_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
+                cudaStreamSynchronize(m->st) != cudaSuccess) {
+                set_error("reading the convergence metric failed: %s", cudaGetErrorString(cudaGetLastError()));
+                st = LOC_ECUDA;
+                break;
+            }
+            memcpy(&dtex, &bits, sizeof(float));
+            if (o->tol_tex > 0.0 && dtex < o->tol_tex) { converged = true; it++; break; }
+        }
+    }
+    cudaEventRecord(e1, m->st);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LOC_OK) return st;
+    if (ce != cudaSuccess) { set_error("iteration failed: %s", cudaGetErrorString(ce)); return LOC_ECUDA; }
+    if (r) {
+        r->iterations = it;
+        r->max_rel_dtex = dtex;
+        if (m->segs_per_sim < 0) r->segments = -1;
+        else r->segments = m->segs_per_sim;
+        r->updates = (m->segs_per_sim > 0 ? (double)m->segs_per_sim : 0.0) * D.n_ch * D.T * it;
+        r->kernel_ms = ms;
+        unsigned long long mc = 0;
+        cudaMemcpy(&mc, D.maser_count, sizeof(mc), cudaMemcpyDeviceToHost);
+        r->n_maser_cells = (int64_t)mc;
+    }
+    if (o->tol_tex > 0.0 && !converged) {
+        set_error("not converged: max |dTex/Tex| = %g after %d iterations", dtex, it);
+        return LOC_ENOTCONV;
+    }
+    return LOC_OK;
+}
+
+loc_status loc_get_radiation(const loc_model *m, double *sij, double *esc, double *norm,
+                             size_t n_lc, size_t n_c)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    if (!m->has_rad) { set_error("no ray simulation has run"); return LOC_ESTATE; }
+    const DevModel &D = m->d;
+    const size_t nlc = (size_t)D.T * D.n_cells;
+    if ((sij || esc) && n_lc < nlc) { set_error("sij/esc buffers need %zu elements", nlc); return LOC_EINVAL; }
+    if (norm && n_c < (size_t)D.n_cells) { set_error("norm buffer needs %lld elements", D.n_cells); return LOC_EINVAL; }
+    double *buf = nullptr;
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(double) * (2 * nlc + D.n_cells)));
+    loc_status s = launch_acc_to_f64(D, m->last_fp64, buf, buf + nlc, buf + 2 * nlc, m->st);
+    if (s == LOC_OK) {
+        cudaError_t e = cudaSuccess;
+        if (sij) e = cudaMemcpyAsync(sij, buf, sizeof(double) * nlc, cudaMemcpyDeviceToHost, m->st);
+        if (esc && e == cudaSuccess) e = cudaMemcpyAsync(esc, buf + nlc, sizeof(double) * nlc, cudaMemcpyDeviceToHost, m->st);
+        if (norm && e == cudaSuccess) e = cudaMemcpyAsync(norm, buf + 2 * nlc, sizeof(double) * D.n_cells, cudaMemcpyDeviceToHost, m->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+        if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    }
+    cudaFree(buf);
+    return s;
+}
+
+loc_status loc_get_populations(const loc_model *m, double *out, size_t n_out)
+{
+    if (!m || !out) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
+    const size_t n = (size_t)m->d.n_cells * m->d.L;
+    if (n_out < n) { set_error("output needs %zu elements", n); return LOC_EINVAL; }
+    LOC_CUDA_TRY(cudaMemcpyAsync(out, m->d.x, sizeof(double) * n, cudaMemcpyDeviceToHost, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    return LOC_OK;
+}
+
+loc_status loc_set_populations(loc_model *m, const double *in, size_t n_in)
+{
+    if (!m || !in) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
+    const size_t n = (size_t)m->d.n_cells * m->d.L;
+    if (n_in != n) { set_error("populations need exactly %zu elements", n); return LOC_EINVAL; }
+    if (!finite_pos(in, (long long)n, true)) { set_error("populations must be finite and >= 0"); return LOC_EINVAL; }
+    LOC_CUDA_TRY(cudaMemcpyAsync(m->d.x, in, sizeof(double) * n, cudaMemcpyHostToDevice, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    m->has_rad = false;
+    return LOC_OK;
+}
+
+loc_status loc_get_tex(const loc_model *m, int t, double *out, size_t n_out)
+{
+    if (!m || !out) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
+    if (t < 0 || t >= m->d.T) { set_error("line index %d out of range", t); return LOC_EINVAL; }
+    if (n_out < (size_t)m->d.n_cells) { set_error("output needs %lld elements", m->d.n_cells); return LOC_EINVAL; }
+    double *buf = nullptr;
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(double) * m->d.n_cells));
+    loc_status s = launch_tex(m->d, t, buf, m->st);
+    if (s == LOC_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, buf, sizeof(double) * m->d.n_cells, cudaMemcpyDeviceToHost, m->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+        if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    }
+    cudaFree(buf);
+    return s;
+}
+
+loc_status loc_spectra(const loc_model *m, int t, const double *p_cm, int n_p, double *T_out,
+                       size_t n_out)
+{
+    if (!m || (!p_cm && n_p > 0) || (!T_out && n_p > 0)) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
+    if (m->d.geometry != LOC_SHELLS_1D) { set_error("loc_spectra supports 1D models"); return LOC_EINVAL; }
+    if (t < 0 || t >= m->d.T) { set_error("line index %d out of range", t); return LOC_EINVAL; }
+    if (n_p < 0) { set_error("n_p must be >= 0"); return LOC_EINVAL; }
+    if (n_p == 0) return LOC_OK;
+    const size_t n = (size_t)n_p * m->d.n_ch;
+    if (n_out < n) { set_error("output needs %zu elements", n); return LOC_EINVAL; }
+    for (int i = 0; i < n_p; i++)
+        if (!(p_cm[i] >= 0.0) || !std::isfinite(p_cm[i])) { set_error("impact parameter %d invalid", i); return LOC_EINVAL; }
+    double *pd = nullptr;
+    float *Td = nullptr;
+    LOC_CUDA_TRY(cudaMalloc(&pd, sizeof(double) * n_p));
+    if (cudaMalloc(&Td, sizeof(float) * n) != cudaSuccess) { cudaFree(pd); set_error("allocation failed"); return LOC_ENOMEM; }
+    std::vector<float> tmp(n);
+    loc_status s = LOC_OK;
+    cudaError_t e = cudaMemcpyAsync(pd, p_cm, sizeof(double) * n_p, cudaMemcpyHostToDevice, m->st);
+    if (e == cudaSuccess) {
+        s = launch_line_params(m->d, m->st);
+        if (s == LOC_OK) s = launch_spectra1d(m->d, t, pd, n_p, Td, m->st);
+        if (s == LOC_OK) {
+            e = cudaMemcpyAsync(tmp.data(), Td, sizeof(float) * n, cudaMemcpyDeviceToHost, m->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+        }
+    }
+    if (e != cudaSuccess) { set_error("spectra failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    if (s == LOC_OK) for (size_t i = 0; i < n; i++) T_out[i] = tmp[i];
+    cudaFree(pd);
+    cudaFree(Td);
+    return s;
+}
+
+loc_status loc_model_info(const loc_model *m, int64_t *n_cells, int *n_levels, int *n_lines,
+                          int64_t *segments_per_sim)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    if (n_cells) *n_cells = m->d.n_cells;
+    if (n_levels) *n_levels = m->has_mol ? m->d.L : 0;
+    if (n_lines) *n_lines = m->has_mol ? m->d.T : 0;
+    if (segments_per_sim) *segments_per_sim = m->segs_per_sim;
+    return LOC_OK;
+}
+
+loc_status loc_trace_ray(const loc_model *m, int dir, int64_t i, int64_t j, int64_t *cells,
+                         int64_t *dz, int64_t cap, int64_t *n_seg)
+{
+    if (!m || !n_seg) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (m->d.geometry != LOC_GRID_3D) { set_error("loc_trace_ray needs a 3D grid model"); return LOC_EINVAL; }
+    if (dir < 0 || dir >= m->d.n_dir) { set_error("direction %d out of range", dir); return LOC_EINVAL; }
+    if (i < 0 || j < 0 || i >= m->d.N || j >= m->d.N) { set_error("root line out of range"); return LOC_EINVAL; }
+    if (cap < 0 || (cap > 0 && (!cells || !dz))) { set_error("bad output buffers"); return LOC_EINVAL; }
+    long long *buf = nullptr;
+    const long long dcap = cap > 0 ? cap : 1;
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(long long) * (2 * dcap + 1)));
+    loc_status s = launch_trace3d(m->d, dir, i, j, buf, buf + dcap, dcap, buf + 2 * dcap, m->st);
+    long long n = 0;
+    if (s == LOC_OK) {
+        cudaError_t e = cudaMemcpyAsync(&n, buf + 2 * dcap, sizeof(long long), cudaMemcpyDeviceToHost, m->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+        if (e != cudaSuccess) { set_error("trace failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    }
+    if (s == LOC_OK) {
+        *n_seg = n;
+        if (n > cap) {
+            set_error("ray has %lld segments, capacity %lld", n, (long long)cap);
+            s = LOC_EINVAL;
+        } else if (n > 0) {
+            cudaError_t e = cudaMemcpy(cells, buf, sizeof(long long) * n, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(dz, buf + dcap, sizeof(long long) * n, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+        }
+    }
+    cudaFree(buf);
+    return s;
+}
+
+loc_status loc_sync(loc_model *m)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    return LOC_OK;
+}
+
+void loc_destroy(loc_model *m)
+{
+    if (!m) return;
+    cudaStreamSynchronize(m->st);
+    dev_free_all(m, m->mol_mem);
+    dev_free_all(m, m->geo_mem);
+    delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// loc_internal.cuh -- device-side data layout and shared helpers of the
+// GB300 LOC library.  Everything here is internal to the shared library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/loc.h"
+
+namespace loc {
+
+// CGS constants (CODATA 2018 exact SI values).
+constexpr double kH = 6.62607015e-27;
+constexpr double kKB = 1.380649e-16;
+constexpr double kC = 2.99792458e10;
+constexpr double kAMU = 1.66053906660e-24;
+constexpr double kPI = 3.14159265358979323846;
+
+// One root cell is 2^kFixedBits integer units in the 3D ray geometry.
+constexpr int kFixedBits = 24;
+constexpr int kMaxLevels = 32;      // molecule levels supported by the SE
+constexpr int kMaxLines = 64;       // radiative lines
+constexpr int kMaxChannels = 1024;
+constexpr int kMaxLinesPerWarp = 16;
+
+// One step of a 1D ray through one shell, precomputed at model creation:
+// cell index, path length s (cm), line-of-sight velocity at the step's
+// start (cm/s) and the step's weight w = A_j s / W_c.
+struct Seg1D {
+    int cell;
+    float s;
+    float vlos;
+    float w;
+};
+
+// Per-direction integer description of the 3D ray lattice.
+struct Dir3D {
+    int m, a, b;            // main / transverse axes
+    int flip[3];            // mirrored axes
+    long long qa, qb;       // slopes in units of 2^-F
+    float d[3];             // true unit direction (for v . d)
+    float unit;             // cm per fixed-point unit along the ray
+};
+
+// Device view of one model.  All pointers are device memory.
+struct DevModel {
+    int geometry;
+    long long n_cells;
+    int n_ch;
+    double v_min, dv;
+    double t_bg;
+
+    // static per-cell data
+    double *n_h2, *t_kin, *abundance;   // FP64: line parameters and SE
+    float *inv_s2sig;                   // 1 / (sqrt(2) sigma) per cell
+    float4 *vel;                        // 3D: {vx, vy, vz, inv_s2sig}
+
+    // 1D geometry
+    int K, n_rays;
+    long long n_segs;
+    double *radius;                     // [K]
+    float *v1d;                         // [K] radial velocity
+    int *ray_off;                       // [n_rays + 1]
+    Seg1D *segs;                        // [n_segs]
+
+    // 3D geometry
+    int N, n_dir;
+    double h0;
+    Dir3D *dirs;                        // [n_dir]
+
+    // molecule
+    int L, T, P;
+    double mass_amu;
+    double *energy_K, *g;               // [L]
+    int *line_u, *line_l;               // [T]
+    double *line_A, *line_nu;           // [T]
+    int *coll_u, *coll_l;               // [P]
+    double *coll_k;                     // [P]
+    float *nbg;                         // [T] background occupation
+    double *nbg64;                      // [T]
+
+    // iteration state
+    double *x;                          // [n_cells][L] populations
+    double *x_new;                      // [n_cells][L]
+    float2 *ks;                         // [T][n_cells] {K s-less opacity, S}
+    float2 *acc;                        // [T][n_cells] {SIJ, ESC}
+    float *norm;                        // [n_cells]
+    double *acc64;                      // [T][n_cells][2] (FP64 accumulation)
+    double *norm64;                     // [n_cells]
+    unsigned int *dtex_bits;            // device scalar: max rel dTex (float bits)
+    unsigned long long *maser_count;    // device scalar
+};
+
+// Parameters of one march launch.
+struct MarchArgs {
+    int line0;          // first line of this pass
+    int n_lines;        // lines in this pass
+    float window;       // window half-width in sigma (0 = all channels)
+    int fp64_acc;       // accumulate in FP64
+    int do_norm;        // this pass also accumulates NORM
+};
+
+// ----------------------------------------------------------------------------
+// host-side helpers (implemented in loc_api.cu)
+// ----------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+#define LOC_CUDA_TRY(call)                                                        \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            ::loc::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), \
+                             __FILE__, __LINE__);                                 \
+            return LOC_ECUDA;                                                     \
+        }                                                                         \
+    } while (0)
+
+// kernel launchers (one per translation unit)
+loc_status launch_geom1d(const DevModel &m, cudaStream_t st);
+loc_status launch_line_params(const DevModel &m, cudaStream_t st);
+loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
+loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);
+loc_status launch_lte(const DevModel &m, cudaStream_t st);
+loc_status launch_bg(const DevModel &m, cudaStream_t st);
+loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st);
+loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p,
+                            float *T_dev, cudaStream_t st);
+loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,
+                          long long *cells, long long *dz, long long cap,
+                          long long *n_out, cudaStream_t st);
+loc_status launch_dir_setup(const double *dirs_dev, int n_dir, double h0, Dir3D *out,
+                            cudaStream_t st);
+loc_status launch_cell_setup(const DevModel &m, const double *sigma_turb, const double *vx,
+                             const double *vy, const double *vz, cudaStream_t st);
+loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,
+                             double *norm, cudaStream_t st);
+
+}  // namespace loc
