@@ -1,0 +1,369 @@
+"""Benchmark of the LOC ALI hot path on GB300.
+
+Default workload: the 1D multilevel rotor cloud (256 shells, 12 levels /
+11 lines, 256 channels, seeded lognormal-perturbed power-law density, T_kin
+10-30 K), one step = one complete ALI solve from LTE (50 iterations of line
+parameters -> ray march -> statistical equilibrium) plus the emergent
+spectra of the J=1-0 line at every impact parameter.  Metric: cell-channel
+updates per second (one update = one (ray step, channel, line) application
+of the formal solution; channels skipped by the 8-sigma window count as
+updated, the computed count is reported beside it).
+
+Other workloads (``--workload``): ``twolevel1d`` (32-shell two-level cloud,
+20 iterations) and ``grid3d`` (128^3 regular grid, 48 directions, 128
+channels, one ALI iteration per step).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload (the only other place this script runs
+the oracle is the cpu_baseline leg).
+
+Multi-GPU: one process per GPU under torchrun; the 1D models do not shard,
+so every rank solves its own replica (weak scaling, no collective on the
+data path); the timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import loc_inputs as LI  # noqa: E402
+
+WINDOW = 8.0        # channel window half-width in sigma (I unchanged to FP32 beyond it)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name):
+    if name == "rotor1d":
+        mol = LI.rotor_molecule()
+        model = LI.cloud1d_rotor()
+        return dict(name="1D rotor cloud: 256 shells, 12 levels (11 lines), 256 channels, "
+                         "50 ALI iterations + spectra",
+                    key="rotor1d", mol=mol, model=model, n_iter=50, spectra=True)
+    if name == "twolevel1d":
+        mol = LI.two_level_molecule()
+        model = LI.cloud1d_two_level()
+        return dict(name="1D two-level cloud: 32 shells, 64 channels, 20 ALI iterations + spectra",
+                    key="twolevel1d", mol=mol, model=model, n_iter=20, spectra=True)
+    if name == "grid3d":
+        mol = LI.rotor_molecule()
+        model = LI.grid3d_cloud()
+        return dict(name="3D regular grid 128^3, 12-level rotor (11 lines), 128 channels, "
+                         "48 HEALPix directions, 1 ALI iteration",
+                    key="grid3d", mol=mol, model=model, n_iter=1, spectra=False)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+def oracle_sample(wl, budget_s=15.0):
+    """Times the oracle on a bounded sample of the workload; returns
+    (updates/s, cores, sample description)."""
+    import oracle
+    oracle.build()
+    mol, model = wl["mol"], wl["model"]
+    T = len(mol["line_nu"])
+    nch = model["n_ch"]
+    cores = oracle.n_threads()
+    if model["geometry"] == "shells1d":
+        segs = sum(len(oracle.paths_1d(model, j)[0]) for j in range(model["n_rays"]))
+        x = oracle.lte_populations(mol, model["t_kin"])
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            x, _ = oracle.iterate_1d(mol, model, 1, x0=x)
+            n += 1
+            if time.perf_counter() - t0 > budget_s or n >= wl["n_iter"]:
+                break
+        dt = time.perf_counter() - t0
+        ups = segs * nch * T * n / dt
+        return ups, cores, f"{n} ALI iteration(s) of the full model ({segs} ray steps x {nch} channels x {T} lines each)"
+    # 3D: one direction, a strided subset of root rays
+    N = model["n_root"]
+    stride = 64
+    x = oracle.lte_populations(mol, model["t_kin"])
+    Kp, S = oracle.line_params(mol, model, x)
+    nseg = 0
+    for r in range(0, N * N, stride):
+        nseg += len(oracle.paths_grid3d(N, model["dirs"][0], r // N, r % N)[0])
+    t0 = time.perf_counter()
+    oracle.march_grid3d(mol, model, Kp, S, dir_range=(0, 1), ray_stride=stride)
+    dt = time.perf_counter() - t0
+    ups = nseg * nch * T / dt
+    return ups, cores, f"ray march of direction 0, every {stride}th root ray ({nseg} ray steps x {nch} channels x {T} lines)"
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ups_list = []
+    cores = 0
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        ups, cores, sample = oracle_sample(wl, budget_s=5.0)
+        if i >= args.warmup:
+            ups_list.append(ups)
+    v = statistics.median(ups_list)
+    line = {"impl": "reference", "metric": "cell-channel updates/s", "value": v,
+            "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": {"workload": wl["name"]},
+            "cpu_baseline": {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def _desc_bytes(model, mol):
+    b = 0
+    for v in list(model.values()) + list(mol.values()):
+        if isinstance(v, np.ndarray):
+            b += v.nbytes
+    return b
+
+
+def run_gpu(args, wl):
+    import torch
+    import torch.distributed as dist
+    from paper_2009_12609_gb300 import build, loc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    loc.load()
+    peaks, peak_src = _peaks()
+
+    mol, model = wl["mol"], wl["model"]
+    T = len(mol["line_nu"])
+    nch = model["n_ch"]
+    is1d = model["geometry"] == "shells1d"
+    R = model["radius"][-1] if is1d else None
+    p_spec = np.concatenate([[0.0], (np.arange(model["n_rays"]) + 0.5) * R / model["n_rays"]]) if is1d else None
+    opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW)
+
+    m = loc.Model(model, mol)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(profile=False):
+        m.reset()
+        rep = m.iterate(profile=profile, **opts)
+        if wl["spectra"]:
+            m.spectra(0, p_spec)
+        return rep
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed between steps (outside the step events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    reps = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        reps.append(step(profile=True))
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms_steps = [a.elapsed_time(b) for a, b in evs]
+    ms_total = sum(ms_steps)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+
+    seg = reps[0]["segments"]
+    iters = reps[0]["iterations"]
+    upd_step = seg * nch * T * iters                    # nominal updates per step
+    value = upd_step * args.steps * world / (ms_total / 1e3)
+
+    # dominant kernel: the ray march (CUDA events around every launch, on the
+    # launching stream, inside loc_iterate)
+    march_ms = sum(r["march_ms"] for r in reps)
+    launches = sum(r["march_launches"] for r in reps)
+    comp = sum(r["computed_updates"] for r in reps)
+    se_ms = sum(r["se_ms"] for r in reps)
+    par_ms = sum(r["params_ms"] for r in reps)
+    per_launch_s = march_ms / 1e3 / launches
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # ALU roofline: 10 FP32-pipe operations per computed update at 128 lanes/SM
+    alu_peak = n_sm * 128 * sm_max * 1e6 / 10.0 / 1e9            # Gupd/s
+    achieved = comp / launches / per_launch_s / 1e9               # computed Gupd/s
+    bytes_per_seg = 28 + 24 * T
+    hbm_achieved = seg * bytes_per_seg / per_launch_s / 1e9       # algorithmic GB/s
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupd/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "march1d_kernel" if is1d else "march3d_kernel",
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / 10 ops per update",
+                "hbm_algorithmic_gbs": hbm_achieved,
+                "hbm_frac_of_measured": hbm_achieved / float(peaks["hbm_gbs"]),
+                "march_ms_per_launch": per_launch_s * 1e3,
+                "share_of_step": march_ms / ms_total if world == 1 else None}
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        with loc.Model(model, mol) as me:
+            me.iterate(**opts)
+            x = me.populations()
+            d2h = x.nbytes
+            if wl["spectra"]:
+                sp = me.spectra(0, p_spec)
+                d2h += sp.nbytes
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = upd_step * world / e2e_s if world == 1 else None
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = upd_step * world / float(t.item())
+
+    per_iter_launches = 1 + (T + 15) // 16 + 1
+    gpu_launches = args.steps * (iters * per_iter_launches + (3 if wl["spectra"] else 1))
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            ups, cores, sample = oracle_sample(wl, budget_s=15.0)
+            cpu = {"value": ups, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                   "sample": sample}
+        line = {"metric": "cell-channel updates/s", "value": value, "unit": "updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+                "config": {"workload": wl["name"], "iterations_per_step": iters,
+                           "ray_steps_per_iteration": seg, "channels": nch, "lines": T,
+                           "window_sigmas": WINDOW, "models_per_step": world,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single",
+                           "l2": "flushed (256 MB write) between timed steps"},
+                "computed_updates_per_s": comp * world / (ms_total / 1e3),
+                "models_per_s": world * 1e3 / ms_step,
+                "kernel_ms_per_step": {"march": march_ms / args.steps, "se": se_ms / args.steps,
+                                       "line_params": par_ms / args.steps},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": "updates/s",
+                        "h2d_bytes_per_step": _desc_bytes(model, mol), "d2h_bytes_per_step": d2h},
+                "gpu_launches": gpu_launches, "clocks": clocks,
+                "wall_s_timed": wall, "peak_source": peak_src}
+        print(json.dumps(line))
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rotor1d", choices=["rotor1d", "twolevel1d", "grid3d"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,9 @@ typedef struct loc_molecule_desc {
  *                 time mode is k = 1, Sect. 2).
  *  window_sigmas  0: update every channel; w > 0: skip channels farther
  *                 than w sigma from the local line centre (Sect. A.2).
+ *  profile        1: time every kernel with CUDA events on the model's
+ *                 stream and count the channel updates actually computed
+ *                 (fills the *_ms and computed_updates report fields).
  */
 typedef struct loc_iter_opts {
     int max_iter;
@@ -153,6 +156,7 @@ typedef struct loc_iter_opts {
     int precision;
     int lines_per_pass;
     double window_sigmas;
+    int profile;
 } loc_iter_opts;
 
 /* Iteration report. */
@@ -163,6 +167,12 @@ typedef struct loc_iter_report {
     double updates;            /* (step, channel, line) updates, all iters  */
     double kernel_ms;          /* device time of the iterations (events)    */
     int64_t n_maser_cells;     /* (line, cell) pairs with negative opacity  */
+    /* filled when opts.profile = 1 (0 otherwise) */
+    double march_ms;           /* summed duration of the march launches     */
+    double se_ms;              /* summed duration of the equilibrium solves */
+    double params_ms;          /* summed duration of the line-parameter step*/
+    int64_t march_launches;    /* number of march launches                  */
+    double computed_updates;   /* updates inside the channel windows        */
 } loc_iter_report;
 
 typedef struct loc_model loc_model;
@@ -186,6 +196,10 @@ loc_status loc_set_molecule(loc_model *m, const loc_molecule_desc *mol);
  * statistical-equilibrium solve.  r may be NULL.  Returns LOC_ENOTCONV
  * (with the work done) if tol_tex > 0 was not reached in max_iter. */
 loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r);
+
+/* Reset the populations to LTE at T_kin (the starting point of the
+ * iteration, Sect. 3.3.2) without re-uploading the molecule. */
+loc_status loc_reset_populations(loc_model *m);
 
 /* One ray simulation with the current populations, without the
  * equilibrium solve: fills the per-cell accumulators read by

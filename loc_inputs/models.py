@@ -159,11 +159,14 @@ def _fields3d(N, seed, mean_density=1.0e4, sigma_ln=1.0, v_rms_kms=1.0):
 
 
 def grid3d_cloud(N=128, n_ch=128, seed=SEED_BASE + 2, box_pc=1.0, t_kin=15.0,
-                 abundance=1.0e-4, half_width_kms=3.0, nside=2):
+                 abundance=1.0e-6, half_width_kms=3.0, nside=2):
     """Regular N^3 grid: lognormal density from a -11/3 Gaussian random
     field (sigma_ln 1, mean 1e4 cm^-3), three independent velocity
     components with the same spectrum and 3D rms 1 km/s, T_kin 15 K,
-    sigma_turb 0.2 km/s, 128 channels over +-3 km/s, 48 HEALPix directions."""
+    sigma_turb 0.2 km/s, 128 channels over +-3 km/s, 48 HEALPix directions.
+    Box 1 pc and abundance 1e-6 give the J=1-0 line line-of-sight optical
+    depths of a few on average and up to ~100 through the densest cells
+    (partially optically thick)."""
     n_h2, (vx, vy, vz) = _fields3d(N, seed)
     M = N ** 3
     nch, vmin, dv = _channels(n_ch, half_width_kms)

@@ -144,6 +144,29 @@ __global__ void trace3d_kernel(DevModel m, int dir, long long i, long long j,
     *n_out = n;
 }
 
+// thread per root line: number of segments of one ray simulation
+__global__ void count3d_kernel(DevModel m, unsigned long long *total)
+{
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per_dir = (long long)m.N * m.N;
+    if (item >= per_dir * m.n_dir) return;
+    const int dir = (int)(item / per_dir);
+    const long long r = item - (long long)dir * per_dir;
+    const Dir3D D = m.dirs[dir];
+    unsigned long long n = 0;
+    walk_grid3d(D, m.N, r / m.N, r % m.N, [&](long long, long long) { n++; });
+    atomicAdd(total, n);
+}
+
+loc_status launch_count3d(const DevModel &m, unsigned long long *total_dev, cudaStream_t st)
+{
+    const long long items = (long long)m.N * m.N * m.n_dir;
+    LOC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), st));
+    count3d_kernel<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(m, total_dev);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
 loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,
                           long long *cells, long long *dz, long long cap,
                           long long *n_out, cudaStream_t st)

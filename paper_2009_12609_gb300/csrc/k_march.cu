@@ -60,7 +60,7 @@ __device__ __forceinline__ float warp_sum(float v)
 // Process one step through `cell`.  All lanes call it with identical
 // arguments.  vlos: line-of-sight velocity; inv: 1/(sqrt(2) sigma).
 template <int G>
-__device__ __forceinline__ void march_step(const DevModel &m, const MarchArgs &a, float *I,
+__device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
                                            long long cell, float s, float vlos, float inv,
                                            float w, int lane)
 {
@@ -137,6 +137,14 @@ __device__ __forceinline__ void march_step(const DevModel &m, const MarchArgs &a
             }
         }
     }
+    return khi - klo;
+}
+
+// add this warp's computed-update count (profiling)
+__device__ __forceinline__ void flush_count(const DevModel &m, const MarchArgs &a, long long nw,
+                                            int lane)
+{
+    if (a.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)(nw * a.n_lines));
 }
 
 template <int G>
@@ -161,11 +169,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m
     float *I = smem + (size_t)wid * a.n_lines * m.n_ch;
     init_ray<G>(m, a, I, lane);
     const int s0 = m.ray_off[j], s1 = m.ray_off[j + 1];
+    long long nw = 0;
     for (int si = s0; si < s1; si++) {
         const Seg1D sg = m.segs[si];
-        march_step<G>(m, a, I, sg.cell, sg.s, sg.vlos, m.inv_s2sig[sg.cell], sg.w, lane);
+        nw += march_step<G>(m, a, I, sg.cell, sg.s, sg.vlos, m.inv_s2sig[sg.cell], sg.w, lane);
         __syncwarp();
     }
+    flush_count(m, a, nw, lane);
 }
 
 // 3D regular grid: one warp per (direction, root line).
@@ -185,14 +195,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m
     init_ray<G>(m, a, I, lane);
     const Dir3D D = m.dirs[dir];
     const float wscale = 1.0f / ((float)(1ll << kFixedBits) * (float)m.n_dir);
+    long long nw = 0;
     walk_grid3d(D, m.N, i, j, [&](long long cell, long long dz) {
         const float4 cv = m.vel[cell];
         const float vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
         const float s = (float)dz * D.unit;
         const float w = (float)dz * wscale;
-        march_step<G>(m, a, I, cell, s, vlos, cv.w, w, lane);
+        nw += march_step<G>(m, a, I, cell, s, vlos, cv.w, w, lane);
         __syncwarp();
     });
+    flush_count(m, a, nw, lane);
 }
 
 template <int G>

@@ -196,7 +196,12 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         TRY(upload(m, &dirs, d->dirs, 3 * (size_t)d->n_dir, m->geo_mem, "dirs"));
         TRY(upload<Dir3D>(m, &D.dirs, nullptr, d->n_dir, m->geo_mem, "direction records"));
         TRY(launch_dir_setup(dirs, d->n_dir, d->h0, D.dirs, m->st));
-        m->segs_per_sim = -1;    // counted on demand
+        unsigned long long *cnt = nullptr, total = 0;
+        TRY(upload<unsigned long long>(m, &cnt, nullptr, 1, m->geo_mem, "segment count"));
+        TRY(launch_count3d(D, cnt, m->st));
+        LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        m->segs_per_sim = (long long)total;
     }
     LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
     return LOC_OK;
@@ -279,6 +284,7 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
     TRY(upload<double>(m, &D.norm64, nullptr, nc, m->mol_mem, "norm64"));
     TRY(upload<unsigned int>(m, &D.dtex_bits, nullptr, 1, m->mol_mem, "dtex"));
     TRY(upload<unsigned long long>(m, &D.maser_count, nullptr, 1, m->mol_mem, "maser count"));
+    TRY(upload<unsigned long long>(m, &D.upd_count, nullptr, 1, m->mol_mem, "update count"));
     TRY(launch_cell_setup(D, m->sigma_turb, m->vx, m->vy, m->vz, m->st));
     TRY(launch_bg(D, m->st));
     TRY(launch_lte(D, m->st));
@@ -303,6 +309,15 @@ loc_status loc_set_molecule(loc_model *m, const loc_molecule_desc *mol)
     return LOC_OK;
 }
 
+loc_status loc_reset_populations(loc_model *m)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
+    TRY(launch_lte(m->d, m->st));
+    m->has_rad = false;
+    return LOC_OK;
+}
+
 static loc_status check_opts(const loc_iter_opts *o)
 {
     CHECK(o, "NULL options");
@@ -311,6 +326,7 @@ static loc_status check_opts(const loc_iter_opts *o)
     CHECK(o->precision == LOC_FP32_MARCH || o->precision == LOC_FP64_ACC, "unknown precision");
     CHECK(o->lines_per_pass >= 0, "lines_per_pass must be >= 0");
     CHECK(o->window_sigmas >= 0.0 && std::isfinite(o->window_sigmas), "window_sigmas must be >= 0");
+    CHECK(o->profile == 0 || o->profile == 1, "profile must be 0 or 1");
     return LOC_OK;
 }
 
@@ -335,6 +351,7 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
         a.window = (float)o->window_sigmas;
         a.fp64_acc = fp64;
         a.do_norm = (l0 == 0);
+        a.count = o->profile;
         TRY(launch_march(D, a, m->st));
     }
     m->has_rad = true;
@@ -359,20 +376,38 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     TRY(check_opts(o));
     if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
     DevModel &D = m->d;
+    const bool prof = o->profile == 1;
+    std::vector<cudaEvent_t> ev;              // 4 per iteration when profiling
+    auto mark = [&](size_t idx) -> cudaError_t {
+        if (!prof) return cudaSuccess;
+        while (ev.size() <= idx) {
+            cudaEvent_t e;
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) return ce;
+            ev.push_back(e);
+        }
+        return cudaEventRecord(ev[idx], m->st);
+    };
     cudaEvent_t e0, e1;
     LOC_CUDA_TRY(cudaEventCreate(&e0));
     LOC_CUDA_TRY(cudaEventCreate(&e1));
     LOC_CUDA_TRY(cudaMemsetAsync(D.maser_count, 0, sizeof(unsigned long long), m->st));
+    LOC_CUDA_TRY(cudaMemsetAsync(D.upd_count, 0, sizeof(unsigned long long), m->st));
     LOC_CUDA_TRY(cudaEventRecord(e0, m->st));
     int it = 0;
     float dtex = 0.f;
     bool converged = false;
     loc_status st = LOC_OK;
     for (it = 0; it < o->max_iter; it++) {
+        const size_t b = 4 * (size_t)it;
+        if (mark(b) != cudaSuccess) { st = LOC_ECUDA; break; }
         if ((st = launch_line_params(D, m->st)) != LOC_OK) break;
+        if (mark(b + 1) != cudaSuccess) { st = LOC_ECUDA; break; }
         if ((st = march_impl(m, o)) != LOC_OK) break;
         if (cudaMemsetAsync(D.dtex_bits, 0, sizeof(unsigned), m->st) != cudaSuccess) { st = LOC_ECUDA; break; }
+        if (mark(b + 2) != cudaSuccess) { st = LOC_ECUDA; break; }
         if ((st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st)) != LOC_OK) break;
+        if (mark(b + 3) != cudaSuccess) { st = LOC_ECUDA; break; }
         std::swap(D.x, D.x_new);
         if (o->tol_tex > 0.0 || it == o->max_iter - 1) {
             unsigned bits = 0;
@@ -386,24 +421,46 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
             if (o->tol_tex > 0.0 && dtex < o->tol_tex) { converged = true; it++; break; }
         }
     }
+    if (st == LOC_ECUDA && g_err[0] == 0) set_error("CUDA error in the iteration: %s", cudaGetErrorString(cudaGetLastError()));
     cudaEventRecord(e1, m->st);
     cudaError_t ce = cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    double t_par = 0.0, t_mar = 0.0, t_se = 0.0;
+    if (prof && st == LOC_OK && ce == cudaSuccess) {
+        for (size_t b = 0; b + 3 < ev.size() && b / 4 < (size_t)it; b += 4) {
+            float a = 0.f, c = 0.f, d = 0.f;
+            cudaEventElapsedTime(&a, ev[b], ev[b + 1]);
+            cudaEventElapsedTime(&c, ev[b + 1], ev[b + 2]);
+            cudaEventElapsedTime(&d, ev[b + 2], ev[b + 3]);
+            t_par += a; t_mar += c; t_se += d;
+        }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LOC_OK) return st;
     if (ce != cudaSuccess) { set_error("iteration failed: %s", cudaGetErrorString(ce)); return LOC_ECUDA; }
     if (r) {
+        memset(r, 0, sizeof(*r));
         r->iterations = it;
         r->max_rel_dtex = dtex;
-        if (m->segs_per_sim < 0) r->segments = -1;
-        else r->segments = m->segs_per_sim;
-        r->updates = (m->segs_per_sim > 0 ? (double)m->segs_per_sim : 0.0) * D.n_ch * D.T * it;
+        r->segments = m->segs_per_sim;
+        r->updates = (double)m->segs_per_sim * D.n_ch * D.T * it;
         r->kernel_ms = ms;
-        unsigned long long mc = 0;
+        unsigned long long mc = 0, uc = 0;
         cudaMemcpy(&mc, D.maser_count, sizeof(mc), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&uc, D.upd_count, sizeof(uc), cudaMemcpyDeviceToHost);
         r->n_maser_cells = (int64_t)mc;
+        if (prof) {
+            int per = o->lines_per_pass > 0 ? o->lines_per_pass : D.T;
+            if (per > kMaxLinesPerWarp) per = kMaxLinesPerWarp;
+            r->march_ms = t_mar;
+            r->se_ms = t_se;
+            r->params_ms = t_par;
+            r->march_launches = (int64_t)it * ((D.T + per - 1) / per);
+            r->computed_updates = (double)uc;
+        }
     }
     if (o->tol_tex > 0.0 && !converged) {
         set_error("not converged: max |dTex/Tex| = %g after %d iterations", dtex, it);

@@ -90,6 +90,7 @@ struct DevModel {
     double *norm64;                     // [n_cells]
     unsigned int *dtex_bits;            // device scalar: max rel dTex (float bits)
     unsigned long long *maser_count;    // device scalar
+    unsigned long long *upd_count;      // device scalar: computed updates (profiling)
 };
 
 // Parameters of one march launch.
@@ -99,6 +100,7 @@ struct MarchArgs {
     float window;       // window half-width in sigma (0 = all channels)
     int fp64_acc;       // accumulate in FP64
     int do_norm;        // this pass also accumulates NORM
+    int count;          // count computed channel updates into upd_count
 };
 
 // ----------------------------------------------------------------------------
@@ -128,6 +130,7 @@ loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n
 loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,
                           long long *cells, long long *dz, long long cap,
                           long long *n_out, cudaStream_t st);
+loc_status launch_count3d(const DevModel &m, unsigned long long *total_dev, cudaStream_t st);
 loc_status launch_dir_setup(const double *dirs_dev, int n_dir, double h0, Dir3D *out,
                             cudaStream_t st);
 loc_status launch_cell_setup(const DevModel &m, const double *sigma_turb, const double *vx,

@@ -69,13 +69,17 @@ class loc_molecule_desc(ctypes.Structure):
 class loc_iter_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_tex", ctypes.c_double),
                 ("ali", ctypes.c_int), ("precision", ctypes.c_int),
-                ("lines_per_pass", ctypes.c_int), ("window_sigmas", ctypes.c_double)]
+                ("lines_per_pass", ctypes.c_int), ("window_sigmas", ctypes.c_double),
+                ("profile", ctypes.c_int)]
 
 
 class loc_iter_report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("max_rel_dtex", ctypes.c_double),
                 ("segments", ctypes.c_int64), ("updates", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double), ("n_maser_cells", ctypes.c_int64)]
+                ("kernel_ms", ctypes.c_double), ("n_maser_cells", ctypes.c_int64),
+                ("march_ms", ctypes.c_double), ("se_ms", ctypes.c_double),
+                ("params_ms", ctypes.c_double), ("march_launches", ctypes.c_int64),
+                ("computed_updates", ctypes.c_double)]
 
 
 class LocError(RuntimeError):
@@ -90,7 +94,7 @@ _lib = None
 EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecule",
            "loc_iterate", "loc_march", "loc_get_radiation", "loc_get_populations",
            "loc_set_populations", "loc_get_tex", "loc_spectra", "loc_model_info",
-           "loc_trace_ray", "loc_sync", "loc_destroy"]
+           "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations"]
 
 
 def library_path():
@@ -113,6 +117,7 @@ def load():
     lib.loc_set_molecule.argtypes = [_vp, ctypes.POINTER(loc_molecule_desc)]
     lib.loc_iterate.argtypes = [_vp, ctypes.POINTER(loc_iter_opts), ctypes.POINTER(loc_iter_report)]
     lib.loc_march.argtypes = [_vp, ctypes.POINTER(loc_iter_opts)]
+    lib.loc_reset_populations.argtypes = [_vp]
     lib.loc_get_radiation.argtypes = [_vp, _d, _d, _d, ctypes.c_size_t, ctypes.c_size_t]
     lib.loc_get_populations.argtypes = [_vp, _d, ctypes.c_size_t]
     lib.loc_set_populations.argtypes = [_vp, _d, ctypes.c_size_t]
@@ -236,10 +241,10 @@ def molecule_desc(mol, keep, n_levels=None):
 
 
 def iter_opts(max_iter=1, tol_tex=0.0, ali=True, precision="fp32", lines_per_pass=0,
-              window_sigmas=0.0):
+              window_sigmas=0.0, profile=False):
     prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC}[precision]
     return loc_iter_opts(int(max_iter), float(tol_tex), int(bool(ali)), prec,
-                         int(lines_per_pass), float(window_sigmas))
+                         int(lines_per_pass), float(window_sigmas), int(bool(profile)))
 
 
 # --------------------------------------------------------------------------
@@ -286,7 +291,13 @@ def loc_iterate(h, **opts):
         _check(s)
     return dict(status=s, iterations=r.iterations, max_rel_dtex=r.max_rel_dtex,
                 segments=r.segments, updates=r.updates, kernel_ms=r.kernel_ms,
-                n_maser_cells=r.n_maser_cells)
+                n_maser_cells=r.n_maser_cells, march_ms=r.march_ms, se_ms=r.se_ms,
+                params_ms=r.params_ms, march_launches=r.march_launches,
+                computed_updates=r.computed_updates)
+
+
+def loc_reset_populations(h):
+    _check(load().loc_reset_populations(h))
 
 
 def loc_march(h, **opts):
@@ -371,6 +382,9 @@ class Model:
 
     def iterate(self, **opts):
         return loc_iterate(self.h, **opts)
+
+    def reset(self):
+        loc_reset_populations(self.h)
 
     def march(self, **opts):
         loc_march(self.h, **opts)
