@@ -314,7 +314,7 @@ def run_gpu(args, wl):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_val = upd_step * world / float(t.item())
 
-    per_iter_launches = 1 + (T + 15) // 16 + 1
+    per_iter_launches = 3          # line parameters, march, equilibrium
     gpu_launches = args.steps * (iters * per_iter_launches + (3 if wl["spectra"] else 1))
 
     if rank == 0:

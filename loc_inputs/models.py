@@ -145,8 +145,8 @@ def _grf(rng, N, index=-11.0 / 3.0):
     amp[kk > 0] = kk[kk > 0] ** (index / 2.0)
     g = np.real(np.fft.ifftn(f * amp))
     g -= g.mean()
-    g /= g.std()
-    return g
+    sd = g.std()
+    return g / sd if sd > 0 else np.zeros_like(g)     # N = 1: a uniform field
 
 
 def _fields3d(N, seed, mean_density=1.0e4, sigma_ln=1.0, v_rms_kms=1.0):

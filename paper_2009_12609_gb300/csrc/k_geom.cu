@@ -196,6 +196,15 @@ __global__ void dir_setup_kernel(const double *dirs, int n_dir, double h0, Dir3D
     for (int k = 0; k < 3; k++) { D.flip[k] = d[k] < 0.0; D.d[k] = (float)d[k]; }
     D.qa = (long long)floor(scale * fabs(d[D.a]) / fabs(d[mm]) + 0.5);
     D.qb = (long long)floor(scale * fabs(d[D.b]) / fabs(d[mm]) + 0.5);
+    const unsigned long long H = 1ull << kFixedBits;
+    const unsigned long long step = H << kFixedBits;            // H 2^F
+    const unsigned long long first = (H - H / 2) << kFixedBits; // (H - o) 2^F
+    const unsigned long long qa = D.qa > 0 ? (unsigned long long)D.qa : 1ull;
+    const unsigned long long qb = D.qb > 0 ? (unsigned long long)D.qb : 1ull;
+    D.Da = (long long)(step / qa); D.ra = (long long)(step % qa);
+    D.Db = (long long)(step / qb); D.rb = (long long)(step % qb);
+    D.Qa0 = (long long)(first / qa); D.Ra0 = (long long)(first % qa);
+    D.Qb0 = (long long)(first / qb); D.Rb0 = (long long)(first % qb);
     D.unit = (float)(h0 / scale / fabs(d[mm]));
     out[id] = D;
 }

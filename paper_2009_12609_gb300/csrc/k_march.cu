@@ -11,18 +11,22 @@
 // phi_k f_k = (1 - e^-tau_k) / (K s), the per-channel sums only need
 // t_k = 1 - e^-tau_k and one division per (step, line).
 //
-// GB300 mapping: one warp per ray (and group of lines), lanes over channels,
-// the ray's intensities I[line][channel] in shared memory, profile computed
-// once per step and channel and reused by every line of the group, channels
-// optionally restricted to a window around the local line centre (Sect.
-// A.2), per-step sums reduced across the warp and added to the cell with one
-// vector atomic {SIJ, ESC} per line (FP32) or FP64 atomics.
+// GB300 mapping: one warp per ray (and group of at most 15 lines), lanes
+// over channels, the ray's intensities I[line][channel] in shared memory,
+// the profile computed once per step and channel and reused by every line
+// of the group, channels optionally restricted to a window around the local
+// line centre (Sect. A.2).  The per-step sums {SIJ_t, ESC_t, NORM} of all
+// lanes are combined by a transpose-reduction that leaves line t's totals
+// in lane t, so each step ends with one coalesced vector atomic {SIJ, ESC}
+// per line into the cell's contiguous [cell][line] record.  The next step's
+// cell data is loaded while the current step computes.
 #include "loc_internal.cuh"
 #include "walk3d.cuh"
 
 namespace loc {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr unsigned kFull = 0xffffffffu;
 
 // Channel fraction of a Gaussian between b0 and b0 + db (arguments in units
 // of sqrt(2) sigma), written with upper tails so both wings keep relative
@@ -35,62 +39,86 @@ __device__ __forceinline__ float chan_phi(float b0, float db)
     return (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
 }
 
-// 1 - e^-tau: series for |tau| < 1/8 (truncation < 1e-9 relative), MUFU
-// exponential otherwise.
+// 1 - e^-tau: series for |tau| < 1/8 (truncation < 1e-9 relative), the
+// exponential otherwise; both evaluated, no divergence.
 __device__ __forceinline__ float one_minus_exp(float tau)
 {
-    if (fabsf(tau) < 0.125f) {
-        float p = 1.f - tau * (1.f / 6.f);
-        p = 1.f - tau * (1.f / 5.f) * p;
-        p = 1.f - tau * (1.f / 4.f) * p;
-        p = 1.f - tau * (1.f / 3.f) * p;
-        p = 1.f - tau * 0.5f * p;
-        return tau * p;
-    }
-    return 1.f - __expf(-tau);
+    float p = 1.f - tau * (1.f / 6.f);
+    p = 1.f - tau * (1.f / 5.f) * p;
+    p = 1.f - tau * (1.f / 4.f) * p;
+    p = 1.f - tau * (1.f / 3.f) * p;
+    p = 1.f - tau * 0.5f * p;
+    const float e = __expf(-tau);
+    return (fabsf(tau) < 0.125f) ? tau * p : 1.f - e;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
     return v;
 }
 
-// Process one step through `cell`.  All lanes call it with identical
-// arguments.  vlos: line-of-sight velocity; inv: 1/(sqrt(2) sigma).
+// Sum of v[i] over the 32 lanes for all i at once; lane l receives the
+// total of index l (recursive halving: 31 shuffles for 32 values).
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < m; i++) {
+            const float send = up ? v[i] : v[i + m];
+            const float keep = up ? v[i + m] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, m);
+        }
+    }
+    return v[0];
+}
+
+// Data of one ray step.
+template <int G>
+struct Step {
+    long long cell;
+    float s, w;          // path length (cm), weight of the step
+    float vlos, inv;     // line-of-sight velocity, 1/(sqrt(2) sigma)
+    float2 ks[G];        // {K, S} of the lines of this pass
+};
+
+template <int G>
+__device__ __forceinline__ void load_lines(const DevModel &m, const MarchArgs &a, Step<G> &st)
+{
+    const float2 *p = m.ks + st.cell * m.T + a.line0;
+#pragma unroll
+    for (int t = 0; t < G; t++) st.ks[t] = (t < a.n_lines) ? p[t] : make_float2(0.f, 0.f);
+}
+
+// Process one step.  All lanes call it with identical arguments.  Returns
+// the number of channels computed.
 template <int G>
 __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
-                                           long long cell, float s, float vlos, float inv,
-                                           float w, int lane)
+                                          const Step<G> &st, int lane)
 {
     const int nch = m.n_ch;
     const float dv = (float)m.dv;
-    const float u0 = ((float)m.v_min + vlos) / dv;   // channel coordinate offset
-    const float db = dv * inv;                        // channel width in b units
+    const float u0 = ((float)m.v_min + st.vlos) / dv;   // channel coordinate offset
+    const float db = dv * st.inv;                        // channel width in b units
     int klo = 0, khi = nch;
     if (a.window > 0.f) {
-        const float hw = a.window / (1.41421356f * db);   // window half-width, channels
+        const float hw = a.window / (1.41421356f * db);  // window half-width, channels
         const float cen = -u0;
         klo = (int)fminf(fmaxf(floorf(cen - hw), 0.f), (float)nch);
         khi = (int)fminf(fmaxf(ceilf(cen + hw), 0.f), (float)nch);
     }
-    float Ks[G], Sv[G], sij[G], esc[G];
+    float Ks[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
+        float k = st.ks[t].x * st.s;
+        // keep |K s| >= 1e-20 so that (1 - e^-tau) / (K s) stays phi
+        if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
+        Ks[t] = k;
         sij[t] = 0.f;
         esc[t] = 0.f;
-        if (t < a.n_lines) {
-            const float2 ks = m.ks[(long long)(a.line0 + t) * m.n_cells + cell];
-            float k = ks.x * s;
-            // keep |K s| >= 1e-20 so that (1 - e^-tau) / (K s) stays phi
-            if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
-            Ks[t] = k;
-            Sv[t] = ks.y;
-        } else {
-            Ks[t] = 1e-20f;
-            Sv[t] = 0.f;
-        }
     }
     float nrm = 0.f;
     for (int base = klo; base < khi; base += 32) {
@@ -106,45 +134,53 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
                     const float iv = *ip;
                     sij[t] = fmaf(iv, tm, sij[t]);
                     esc[t] += tm;
-                    *ip = fmaf(Sv[t] - iv, tm, iv);
+                    *ip = fmaf(st.ks[t].y - iv, tm, iv);
                 }
             }
         }
     }
-    // reduce across lanes; lane t adds line t
-    if (a.do_norm) {
-        nrm = warp_sum(nrm);
-        if (lane == 31) {
-            if (a.fp64_acc) atomicAdd(m.norm64 + cell, (double)w * (double)nrm);
-            else atomicAdd(m.norm + cell, w * nrm);
-        }
-    }
+    // lane t < n_lines ends with line t's {SIJ, ESC}; lane 15 with NORM
+    float my_sij, my_esc, my_nrm;
+    if (G <= 2) {
+        my_sij = 0.f;
+        my_esc = 0.f;
 #pragma unroll
-    for (int t = 0; t < G; t++) {
-        if (t < a.n_lines) {
-            const float ss = warp_sum(sij[t]);
-            const float se = warp_sum(esc[t]);
-            if (lane == t) {
-                const float f = w / Ks[t];
-                const long long o = (long long)(a.line0 + t) * m.n_cells + cell;
-                if (a.fp64_acc) {
-                    const double fd = (double)w / (double)Ks[t];
-                    atomicAdd(m.acc64 + 2 * o, fd * (double)ss);
-                    atomicAdd(m.acc64 + 2 * o + 1, fd * (double)se);
-                } else {
-                    atomicAdd(m.acc + o, make_float2(ss * f, se * f));
-                }
-            }
+        for (int t = 0; t < G; t++) {
+            const float a1 = warp_sum(sij[t]), a2 = warp_sum(esc[t]);
+            if (lane == t) { my_sij = a1; my_esc = a2; }
+        }
+        my_nrm = a.do_norm ? warp_sum(nrm) : 0.f;
+    } else {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = 0.f;
+#pragma unroll
+        for (int t = 0; t < G; t++) { v[t] = sij[t]; v[16 + t] = esc[t]; }
+        v[15] = nrm;
+        const float r = transpose_reduce32(v, lane);
+        my_sij = r;
+        my_esc = __shfl_down_sync(kFull, r, 16);
+        my_nrm = r;   // meaningful in lane 15
+    }
+    if (a.do_norm && lane == 15) {
+        if (a.fp64_acc) atomicAdd(m.norm64 + st.cell, (double)st.w * (double)my_nrm);
+        else atomicAdd(m.norm + st.cell, st.w * my_nrm);
+    }
+    if (lane < a.n_lines) {
+        float my_ks = 1.f;
+#pragma unroll
+        for (int t = 0; t < G; t++) if (lane == t) my_ks = Ks[t];
+        const long long o = st.cell * m.T + a.line0 + lane;
+        if (a.fp64_acc) {
+            const double f = (double)st.w / (double)my_ks;
+            atomicAdd(m.acc64 + 2 * o, f * (double)my_sij);
+            atomicAdd(m.acc64 + 2 * o + 1, f * (double)my_esc);
+        } else {
+            const float f = st.w / my_ks;
+            atomicAdd(m.acc + o, make_float2(my_sij * f, my_esc * f));
         }
     }
     return khi - klo;
-}
-
-// add this warp's computed-update count (profiling)
-__device__ __forceinline__ void flush_count(const DevModel &m, const MarchArgs &a, long long nw,
-                                            int lane)
-{
-    if (a.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)(nw * a.n_lines));
 }
 
 template <int G>
@@ -157,63 +193,116 @@ __device__ __forceinline__ void init_ray(const DevModel &m, const MarchArgs &a, 
     __syncwarp();
 }
 
-// 1D shells: one warp per equidistant ray j.
-template <int G>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m, MarchArgs a)
+// add this warp's computed-update count (profiling)
+__device__ __forceinline__ void flush_count(const DevModel &m, const MarchArgs &a, long long nw,
+                                            int lane)
 {
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int j = blockIdx.x * kWarpsPerBlock + wid;
-    if (j >= m.n_rays) return;
-    float *I = smem + (size_t)wid * a.n_lines * m.n_ch;
-    init_ray<G>(m, a, I, lane);
-    const int s0 = m.ray_off[j], s1 = m.ray_off[j + 1];
-    long long nw = 0;
-    for (int si = s0; si < s1; si++) {
-        const Seg1D sg = m.segs[si];
-        nw += march_step<G>(m, a, I, sg.cell, sg.s, sg.vlos, m.inv_s2sig[sg.cell], sg.w, lane);
-        __syncwarp();
-    }
-    flush_count(m, a, nw, lane);
+    if (a.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)(nw * a.n_lines));
 }
 
-// 3D regular grid: one warp per (direction, root line).
+// 1D shells: one warp per (equidistant ray j, line group).  Step records
+// are fetched 32 at a time (one coalesced load) and broadcast by shuffle.
+// The work item of a warp is (ray, line group); the group fixes line0 and
+// n_lines, and group 0 also accumulates NORM.
+__device__ __forceinline__ MarchArgs warp_args(const DevModel &m, MarchArgs a, int g)
+{
+    a.line0 = g * a.per;
+    a.n_lines = min(a.per, m.T - a.line0);
+    a.do_norm = (g == 0);
+    return a;
+}
+
 template <int G>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m, MarchArgs a)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const long long item = (long long)blockIdx.x * kWarpsPerBlock + wid;
+    if (item >= (long long)m.n_rays * a0.n_groups) return;
+    const int j = (int)(item / a0.n_groups);
+    const MarchArgs a = warp_args(m, a0, (int)(item - (long long)j * a0.n_groups));
+    float *I = smem + (size_t)wid * a.per * m.n_ch;
+    init_ray<G>(m, a, I, lane);
+    const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
+    if (n <= 0) return;
+    Seg1D rec = {0, 0.f, 0.f, 0.f};
+    // step q of the ray (0 <= q < n); a new block of 32 records every 32 steps
+    auto fetch = [&](int q, Step<G> &st) {
+        const int r = q & 31;
+        if (r == 0 && q + lane < n) rec = m.segs[s0 + q + lane];
+        st.cell = __shfl_sync(kFull, rec.cell, r);
+        st.s = __shfl_sync(kFull, rec.s, r);
+        st.vlos = __shfl_sync(kFull, rec.vlos, r);
+        st.w = __shfl_sync(kFull, rec.w, r);
+        st.inv = m.inv_s2sig[st.cell];
+        load_lines<G>(m, a, st);
+    };
+    long long nw = 0;
+    Step<G> cur, nxt;
+    fetch(0, cur);
+    for (int q = 0; q < n; q++) {
+        const bool more = q + 1 < n;
+        if (more) fetch(q + 1, nxt);
+        nw += march_step<G>(m, a, I, cur, lane);
+        __syncwarp();
+        if (more) cur = nxt;
+    }
+    flush_count(m, a, nw, lane);
+}
+
+// 3D regular grid: one warp per (direction, root line, line group).
+template <int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m, MarchArgs a0)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const long long item0 = (long long)blockIdx.x * kWarpsPerBlock + wid;
     const long long per_dir = (long long)m.N * m.N;
-    if (item >= per_dir * m.n_dir) return;
+    if (item0 >= per_dir * m.n_dir * a0.n_groups) return;
+    const long long item = item0 / a0.n_groups;
+    const MarchArgs a = warp_args(m, a0, (int)(item0 - item * a0.n_groups));
     const int dir = (int)(item / per_dir);
     const long long r = item - (long long)dir * per_dir;
     const long long i = r / m.N, j = r - (r / m.N) * m.N;
-    float *I = smem + (size_t)wid * a.n_lines * m.n_ch;
+    float *I = smem + (size_t)wid * a.per * m.n_ch;
     init_ray<G>(m, a, I, lane);
     const Dir3D D = m.dirs[dir];
     const float wscale = 1.0f / ((float)(1ll << kFixedBits) * (float)m.n_dir);
+    GridWalk wk;
+    wk.init(D, i, j);
+    auto fetch = [&](Step<G> &st) {
+        long long dz;
+        wk.step(D, m.N, st.cell, dz);
+        const float4 cv = m.vel[st.cell];
+        st.vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
+        st.inv = cv.w;
+        st.s = (float)dz * D.unit;
+        st.w = (float)dz * wscale;
+        load_lines<G>(m, a, st);
+    };
     long long nw = 0;
-    walk_grid3d(D, m.N, i, j, [&](long long cell, long long dz) {
-        const float4 cv = m.vel[cell];
-        const float vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
-        const float s = (float)dz * D.unit;
-        const float w = (float)dz * wscale;
-        nw += march_step<G>(m, a, I, cell, s, vlos, cv.w, w, lane);
+    Step<G> cur, nxt;
+    fetch(cur);
+    while (true) {
+        const bool more = !wk.done(m.N);
+        if (more) fetch(nxt);
+        nw += march_step<G>(m, a, I, cur, lane);
         __syncwarp();
-    });
+        if (!more) break;
+        cur = nxt;
+    }
     flush_count(m, a, nw, lane);
 }
 
 template <int G>
 static loc_status launch_march_g(const DevModel &m, const MarchArgs &a, cudaStream_t st)
 {
-    const size_t smem = (size_t)kWarpsPerBlock * a.n_lines * m.n_ch * sizeof(float);
+    const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
     long long items;
-    if (m.geometry == LOC_SHELLS_1D) items = m.n_rays;
-    else items = (long long)m.N * m.N * m.n_dir;
+    if (m.geometry == LOC_SHELLS_1D) items = (long long)m.n_rays * a.n_groups;
+    else items = (long long)m.N * m.N * m.n_dir * a.n_groups;
     const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (m.geometry == LOC_SHELLS_1D) {
         LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -228,18 +317,19 @@ static loc_status launch_march_g(const DevModel &m, const MarchArgs &a, cudaStre
 
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st)
 {
-    const size_t smem = (size_t)kWarpsPerBlock * a.n_lines * m.n_ch * sizeof(float);
-    if (smem > 227 * 1024) {
-        set_error("march: %d lines x %d channels need %zu B of shared memory per block",
-                  a.n_lines, m.n_ch, smem);
+    const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+    if (smem > 227 * 1024 || a.per > kMaxLinesPerWarp || a.per < 1 ||
+        a.n_groups != (m.T + a.per - 1) / a.per) {
+        set_error("march: %d lines per warp x %d channels need %zu B of shared memory per block",
+                  a.per, m.n_ch, smem);
         return LOC_EINVAL;
     }
-    if (a.n_lines <= 1) return launch_march_g<1>(m, a, st);
-    if (a.n_lines <= 2) return launch_march_g<2>(m, a, st);
-    if (a.n_lines <= 4) return launch_march_g<4>(m, a, st);
-    if (a.n_lines <= 8) return launch_march_g<8>(m, a, st);
-    if (a.n_lines <= 12) return launch_march_g<12>(m, a, st);
-    return launch_march_g<16>(m, a, st);
+    if (a.per <= 1) return launch_march_g<1>(m, a, st);
+    if (a.per <= 2) return launch_march_g<2>(m, a, st);
+    if (a.per <= 4) return launch_march_g<4>(m, a, st);
+    if (a.per <= 8) return launch_march_g<8>(m, a, st);
+    if (a.per <= 12) return launch_march_g<12>(m, a, st);
+    return launch_march_g<15>(m, a, st);
 }
 
 // ----------------------------------------------------------------------------
@@ -293,7 +383,7 @@ __global__ void spectra1d_kernel(DevModel m, int t, const double *pv, int n_p, f
         const float inv = m.inv_s2sig[k];
         const float u0 = ((float)m.v_min + vlos) / dv;
         const float db = dv * inv;
-        const float2 ks = m.ks[(long long)t * m.n_cells + k];
+        const float2 ks = m.ks[(long long)k * m.T + t];
         const float Ksv = ks.x * (float)s;
         const float src = ks.y - nb;
 #pragma unroll

@@ -66,8 +66,8 @@ __global__ void line_params_kernel(DevModel m)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)m.T * m.n_cells) return;
-    const int t = (int)(idx / m.n_cells);
-    const long long c = idx - (long long)t * m.n_cells;
+    const long long c = idx / m.T;                 // layout [cell][line]
+    const int t = (int)(idx - c * m.T);
     const int u = m.line_u[t], l = m.line_l[t];
     const double nu = m.line_nu[t];
     const double gu = m.g[u], gl = m.g[l];
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(128) se_kernel(DevModel m, int ali, int fp64_a
         for (int t = 0; t < m.T; t++) {
             const int u = m.line_u[t], l = m.line_l[t];
             const double A = m.line_A[t];
-            const long long o = (long long)t * m.n_cells + c;
+            const long long o = c * m.T + t;
             double J, beta;
             if (nrm > 0.0) {
                 double s, e;
@@ -219,14 +219,17 @@ __global__ void acc_to_f64_kernel(DevModel m, int fp64_acc, double *sij, double 
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)m.T * m.n_cells;
-    if (idx < n) {
+    if (idx < n) {                               // idx = c * T + t -> out[t][c]
+        const long long c = idx / m.T;
+        const long long t = idx - c * m.T;
+        const long long o = t * m.n_cells + c;
         if (fp64_acc) {
-            if (sij) sij[idx] = m.acc64[2 * idx];
-            if (esc) esc[idx] = m.acc64[2 * idx + 1];
+            if (sij) sij[o] = m.acc64[2 * idx];
+            if (esc) esc[o] = m.acc64[2 * idx + 1];
         } else {
             const float2 a = m.acc[idx];
-            if (sij) sij[idx] = a.x;
-            if (esc) esc[idx] = a.y;
+            if (sij) sij[o] = a.x;
+            if (esc) esc[o] = a.y;
         }
     }
     if (idx < m.n_cells && norm) norm[idx] = fp64_acc ? m.norm64[idx] : (double)m.norm[idx];

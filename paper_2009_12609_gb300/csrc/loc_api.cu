@@ -40,6 +40,7 @@ struct loc_model {
     bool has_rad = false;
     int last_fp64 = 0;
     long long segs_per_sim = 0;
+    int n_sm = 152;
 };
 
 static void *dev_alloc(loc_model *m, size_t bytes, std::vector<void *> &owner)
@@ -214,6 +215,13 @@ loc_status loc_create_model(loc_model **out, const loc_model_desc *d)
     loc_model *m = new (std::nothrow) loc_model();
     if (!m) { set_error("host allocation failed"); return LOC_ENOMEM; }
     m->st = (cudaStream_t)d->stream;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            m->n_sm = nsm;
+        cudaGetLastError();
+    }
     if (d->allocator) {
         if (!d->allocator->alloc || !d->allocator->free) {
             delete m;
@@ -330,7 +338,28 @@ static loc_status check_opts(const loc_iter_opts *o)
     return LOC_OK;
 }
 
-// one ray simulation: zero the accumulators, then one march per line group
+// lines per warp: the requested group size, or (0) all lines when the
+// launch has enough rays to fill the GPU, otherwise smaller groups so that
+// more warps share each ray's lines
+static int lines_per_warp(const loc_model *m, const loc_iter_opts *o)
+{
+    const DevModel &D = m->d;
+    int per = o->lines_per_pass > 0 ? o->lines_per_pass : D.T;
+    if (per > kMaxLinesPerWarp) per = kMaxLinesPerWarp;
+    if (per > D.T) per = D.T;
+    if (o->lines_per_pass == 0) {
+        const long long items = (D.geometry == LOC_SHELLS_1D) ? (long long)D.n_rays
+                                                              : (long long)D.N * D.N * D.n_dir;
+        const long long target = 32ll * m->n_sm;
+        while (per > 1 && items * ((D.T + per - 1) / per) < target) per = (per + 1) / 2;
+    }
+    // shared memory: 4 warps x per x n_ch floats per block
+    while (per > 1 && 4ll * per * D.n_ch * 4 > 200 * 1024) per--;
+    return per;
+}
+
+// one ray simulation: zero the accumulators, then one march launch over
+// all (ray, line group) work items
 static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
 {
     DevModel &D = m->d;
@@ -342,18 +371,14 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
         LOC_CUDA_TRY(cudaMemsetAsync(D.acc, 0, sizeof(float2) * D.T * D.n_cells, m->st));
         LOC_CUDA_TRY(cudaMemsetAsync(D.norm, 0, sizeof(float) * D.n_cells, m->st));
     }
-    int per = o->lines_per_pass > 0 ? o->lines_per_pass : D.T;
-    if (per > kMaxLinesPerWarp) per = kMaxLinesPerWarp;
-    for (int l0 = 0; l0 < D.T; l0 += per) {
-        MarchArgs a;
-        a.line0 = l0;
-        a.n_lines = (D.T - l0 < per) ? D.T - l0 : per;
-        a.window = (float)o->window_sigmas;
-        a.fp64_acc = fp64;
-        a.do_norm = (l0 == 0);
-        a.count = o->profile;
-        TRY(launch_march(D, a, m->st));
-    }
+    MarchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.per = lines_per_warp(m, o);
+    a.n_groups = (D.T + a.per - 1) / a.per;
+    a.window = (float)o->window_sigmas;
+    a.fp64_acc = fp64;
+    a.count = o->profile;
+    TRY(launch_march(D, a, m->st));
     m->has_rad = true;
     m->last_fp64 = fp64;
     return LOC_OK;
@@ -453,12 +478,10 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         cudaMemcpy(&uc, D.upd_count, sizeof(uc), cudaMemcpyDeviceToHost);
         r->n_maser_cells = (int64_t)mc;
         if (prof) {
-            int per = o->lines_per_pass > 0 ? o->lines_per_pass : D.T;
-            if (per > kMaxLinesPerWarp) per = kMaxLinesPerWarp;
             r->march_ms = t_mar;
             r->se_ms = t_se;
             r->params_ms = t_par;
-            r->march_launches = (int64_t)it * ((D.T + per - 1) / per);
+            r->march_launches = (int64_t)it;
             r->computed_updates = (double)uc;
         }
     }

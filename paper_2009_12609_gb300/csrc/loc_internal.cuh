@@ -22,7 +22,7 @@ constexpr int kFixedBits = 24;
 constexpr int kMaxLevels = 32;      // molecule levels supported by the SE
 constexpr int kMaxLines = 64;       // radiative lines
 constexpr int kMaxChannels = 1024;
-constexpr int kMaxLinesPerWarp = 16;
+constexpr int kMaxLinesPerWarp = 15;
 
 // One step of a 1D ray through one shell, precomputed at model creation:
 // cell index, path length s (cm), line-of-sight velocity at the step's
@@ -39,6 +39,8 @@ struct Dir3D {
     int m, a, b;            // main / transverse axes
     int flip[3];            // mirrored axes
     long long qa, qb;       // slopes in units of 2^-F
+    long long Da, ra, Db, rb;       // H 2^F = D q + r (crossing increments)
+    long long Qa0, Ra0, Qb0, Rb0;   // first target (H/2) 2^F = Q q + R
     float d[3];             // true unit direction (for v . d)
     float unit;             // cm per fixed-point unit along the ray
 };
@@ -83,10 +85,10 @@ struct DevModel {
     // iteration state
     double *x;                          // [n_cells][L] populations
     double *x_new;                      // [n_cells][L]
-    float2 *ks;                         // [T][n_cells] {K s-less opacity, S}
-    float2 *acc;                        // [T][n_cells] {SIJ, ESC}
+    float2 *ks;                         // [n_cells][T] {K (per unit phi and length), S}
+    float2 *acc;                        // [n_cells][T] {SIJ, ESC}
     float *norm;                        // [n_cells]
-    double *acc64;                      // [T][n_cells][2] (FP64 accumulation)
+    double *acc64;                      // [n_cells][T][2] (FP64 accumulation)
     double *norm64;                     // [n_cells]
     unsigned int *dtex_bits;            // device scalar: max rel dTex (float bits)
     unsigned long long *maser_count;    // device scalar
@@ -95,11 +97,13 @@ struct DevModel {
 
 // Parameters of one march launch.
 struct MarchArgs {
-    int line0;          // first line of this pass
-    int n_lines;        // lines in this pass
+    int per;            // lines per warp (line group size)
+    int n_groups;       // line groups: a work item is (ray, group)
+    int line0;          // first line of the warp's group (set per warp)
+    int n_lines;        // lines in the warp's group (set per warp)
     float window;       // window half-width in sigma (0 = all channels)
     int fp64_acc;       // accumulate in FP64
-    int do_norm;        // this pass also accumulates NORM
+    int do_norm;        // the warp also accumulates NORM (group 0)
     int count;          // count computed channel updates into upd_count
 };
 

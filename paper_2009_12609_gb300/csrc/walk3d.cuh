@@ -7,38 +7,43 @@
 // through A(z) = o + i H + floor(q_a z / 2^F) (mod N H), likewise B(z), with
 // o = H / 2.  A segment is a maximal run of integer z inside one cell.
 // Because q <= 2^F the transverse coordinate moves by at most one unit per
-// unit of z, so boundaries are met one at a time and the next crossing of a
-// boundary at offset `target` is z = ceil(target 2^F / q).
+// unit of z, so boundaries are met one at a time; the crossing of the
+// boundary at offset `target` is z = ceil(target 2^F / q).  Successive
+// targets differ by H, so the walk carries the quotient and remainder of
+// target 2^F / q and advances them by the per-direction constants
+// H 2^F = D q + r: no division inside the walk.
 #pragma once
 
 #include "loc_internal.cuh"
 
 namespace loc {
 
-__device__ __forceinline__ long long next_cross(long long q, long long target)
-{
-    if (q <= 0) return LLONG_MAX;
-    const unsigned long long num = (unsigned long long)target << kFixedBits;
-    return (long long)((num + (unsigned long long)q - 1ull) / (unsigned long long)q);
-}
+struct GridWalk {
+    long long z, za, zb;        // current z, next a / b crossing
+    long long Qa, Ra, Qb, Rb;   // quotient / remainder of the current targets
+    int ia, ib, im;             // (mirrored) cell indices along a, b, main
 
-// Walks root line (i, j) of direction D on an N^3 grid and calls
-// f(cell, dz) for every segment in order.  All lanes of a warp may run it
-// redundantly (uniform control flow).
-template <class F>
-__device__ __forceinline__ void walk_grid3d(const Dir3D &D, int N, long long i, long long j, F &&f)
-{
-    const long long H = 1ll << kFixedBits;
-    const long long E = (long long)N * H;
-    const long long o = H >> 1;
-    long long ta = H - o;           // next a-boundary, relative to A(0)
-    long long tb = H - o;
-    long long za = next_cross(D.qa, ta);
-    long long zb = next_cross(D.qb, tb);
-    int ia = (int)i, ib = (int)j, im = 0;   // (o + i H) / H = i
-    long long z = 0;
-    while (z < E) {
-        const long long zm = (long long)(im + 1) * H;
+    __device__ __forceinline__ void init(const Dir3D &D, long long i, long long j)
+    {
+        z = 0;
+        ia = (int)i;
+        ib = (int)j;
+        im = 0;
+        Qa = D.Qa0; Ra = D.Ra0;
+        Qb = D.Qb0; Rb = D.Rb0;
+        za = (D.qa > 0) ? Qa + (Ra > 0) : LLONG_MAX;
+        zb = (D.qb > 0) ? Qb + (Rb > 0) : LLONG_MAX;
+    }
+
+    __device__ __forceinline__ bool done(int N) const
+    {
+        return z >= ((long long)N << kFixedBits);
+    }
+
+    // Current segment's cell (x fastest) and length; advances the walk.
+    __device__ __forceinline__ void step(const Dir3D &D, int N, long long &cell, long long &dz)
+    {
+        const long long zm = (long long)(im + 1) << kFixedBits;
         long long zn = zm;
         if (za < zn) zn = za;
         if (zb < zn) zn = zb;
@@ -49,12 +54,35 @@ __device__ __forceinline__ void walk_grid3d(const Dir3D &D, int N, long long i, 
         const int ix = D.flip[0] ? N - 1 - idx[0] : idx[0];
         const int iy = D.flip[1] ? N - 1 - idx[1] : idx[1];
         const int iz = D.flip[2] ? N - 1 - idx[2] : idx[2];
-        const long long cell = ((long long)iz * N + iy) * N + ix;
-        f(cell, zn - z);
+        cell = ((long long)iz * N + iy) * N + ix;
+        dz = zn - z;
         z = zn;
         if (z == zm) im++;
-        if (z == za) { ia = (ia + 1 == N) ? 0 : ia + 1; ta += H; za = next_cross(D.qa, ta); }
-        if (z == zb) { ib = (ib + 1 == N) ? 0 : ib + 1; tb += H; zb = next_cross(D.qb, tb); }
+        if (z == za) {
+            ia = (ia + 1 == N) ? 0 : ia + 1;
+            Qa += D.Da; Ra += D.ra;
+            if (Ra >= D.qa) { Ra -= D.qa; Qa++; }
+            za = Qa + (Ra > 0);
+        }
+        if (z == zb) {
+            ib = (ib + 1 == N) ? 0 : ib + 1;
+            Qb += D.Db; Rb += D.rb;
+            if (Rb >= D.qb) { Rb -= D.qb; Qb++; }
+            zb = Qb + (Rb > 0);
+        }
+    }
+};
+
+// Walks root line (i, j) of direction D and calls f(cell, dz) per segment.
+template <class F>
+__device__ __forceinline__ void walk_grid3d(const Dir3D &D, int N, long long i, long long j, F &&f)
+{
+    GridWalk w;
+    w.init(D, i, j);
+    while (!w.done(N)) {
+        long long c, dz;
+        w.step(D, N, c, dz);
+        f(c, dz);
     }
 }
 
