@@ -243,6 +243,40 @@ loc_status loc_trace_ray(const loc_model *m, int dir, int64_t i, int64_t j,
                          int64_t *cells, int64_t *dz, int64_t cap,
                          int64_t *n_seg);
 
+/*
+ * Radiation field of a 1D model for given line parameters, allocating no
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- a host application whose device
+ * memory belongs to another allocator, or a latency-critical loop in which
+ * cudaMalloc / cudaFree would synchronise the device.
+ *
+ * All pointers are DEVICE pointers owned by the caller:
+ *  radius     [n_shells] FP64 outer radii (cm), strictly increasing
+ *  v_rad      [n_shells] radial velocity (cm/s)
+ *  inv_s2sig  [n_shells] 1 / (sqrt(2) sigma) of the line profile (s/cm)
+ *  ks         [n_shells][n_lines][2] FP32 {K, S}: opacity per unit profile
+ *             fraction and path length, and source function (occupation)
+ *  nbg        [n_lines] background occupation number of each line
+ *  j_ext, beta  outputs [n_shells][n_lines]: J_ext = SIJ / NORM and
+ *             beta = ESC / NORM (background and 1 for a shell no ray crossed)
+ * n_rays = 0 means one ray per shell; the channel grid and window are those
+ * of loc_iter_opts / loc_model_desc.  Limits: n_shells <= 256, n_rays <= 256,
+ * n_lines <= 64, n_ch <= 1024; larger sizes return LOC_EINVAL.
+ * Intermediates live in one fixed 2.5 MiB device array that every GPU which
+ * loads the library keeps until the process exits.  The first call on a
+ * device looks up that array's address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and corrupt each other; serialise them.  The work is
+ * queued on `stream` (cudaStream_t, NULL: legacy default) and the function
+ * returns without waiting for it.
+ */
+loc_status loc_radiation1d_noalloc(int n_shells, int n_rays, const double *radius,
+                                   const float *v_rad, const float *inv_s2sig, int n_ch,
+                                   double v_min, double dv, int n_lines, const float *ks,
+                                   const float *nbg, double window_sigmas, float *j_ext,
+                                   float *beta, void *stream);
+
 /* Wait for all queued work of the model. */
 loc_status loc_sync(loc_model *m);
 

@@ -127,6 +127,17 @@ loc_status launch_geom1d(const DevModel &m, cudaStream_t st)
     return LOC_OK;
 }
 
+// Same set-up with caller-provided temporaries (tan: n_rays ints, W: K
+// doubles) instead of stream-ordered allocations.
+loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W)
+{
+    geom1d_offsets<<<1, 1, 0, st>>>(m, tan);
+    geom1d_weights<<<(m.K + 127) / 128, 128, 0, st>>>(m, tan, W);
+    geom1d_fill<<<(m.n_rays + 127) / 128, 128, 0, st>>>(m, tan, W);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
 // ----------------------------------------------------------------------------
 // 3D: trace one root line and record its segments (tests / diagnostics)
 // ----------------------------------------------------------------------------

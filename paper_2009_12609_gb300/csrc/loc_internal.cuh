@@ -123,6 +123,7 @@ void set_error(const char *fmt, ...);
 
 // kernel launchers (one per translation unit)
 loc_status launch_geom1d(const DevModel &m, cudaStream_t st);
+loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W);
 loc_status launch_line_params(const DevModel &m, cudaStream_t st);
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);

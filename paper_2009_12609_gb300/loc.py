@@ -94,7 +94,8 @@ _lib = None
 EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecule",
            "loc_iterate", "loc_march", "loc_get_radiation", "loc_get_populations",
            "loc_set_populations", "loc_get_tex", "loc_spectra", "loc_model_info",
-           "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations"]
+           "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
+           "loc_radiation1d_noalloc"]
 
 
 def library_path():
@@ -130,6 +131,9 @@ def load():
     lib.loc_sync.argtypes = [_vp]
     lib.loc_destroy.argtypes = [_vp]
     lib.loc_destroy.restype = None
+    lib.loc_radiation1d_noalloc.argtypes = [
+        ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
+        ctypes.c_double, ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]
     _lib = lib
     return lib
 
@@ -358,6 +362,15 @@ def loc_trace_ray(h, d, i, j, cap=1 << 16):
     _check(load().loc_trace_ray(h, int(d), int(i), int(j), cells.ctypes.data_as(_i64),
                                 dz.ctypes.data_as(_i64), cap, ctypes.byref(n)))
     return cells[:n.value].copy(), dz[:n.value].copy()
+
+
+def loc_radiation1d_noalloc(n_shells, n_rays, radius, v_rad, inv_s2sig, n_ch, v_min, dv,
+                            n_lines, ks, nbg, window_sigmas, j_ext, beta, stream=None):
+    """Allocation-free 1D radiation field; every array argument is a device
+    pointer (int) owned by the caller.  Raises LocError on a bad argument."""
+    _check(load().loc_radiation1d_noalloc(
+        int(n_shells), int(n_rays), radius, v_rad, inv_s2sig, int(n_ch), float(v_min),
+        float(dv), int(n_lines), ks, nbg, float(window_sigmas), j_ext, beta, stream))
 
 
 def loc_sync(h):
