@@ -10,7 +10,8 @@
 // velocity at each step's start (Sect. 3.1: Doppler shift at the beginning of
 // the step; the outbound half of the tangent shell starts at cos = 0) and the
 // step's share of the cell's emission, w = A_j s / W_c with
-// W_c = sum over steps in c of A_j s (Sect. 2: sum(s) is known).
+// W_c = sum over steps in c of A_j s (Sect. 2: with deterministic rays the
+// total path length through each cell is available).
 //
 // 3D (Sect. 2.2): per direction the main axis, the mirrored axes and the
 // fixed-point slopes of the ray lattice (see walk3d.cuh).
