@@ -48,7 +48,7 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(name):
+def workload(name, n_root=128):
     if name == "rotor1d":
         mol = LI.rotor_molecule()
         model = LI.cloud1d_rotor()
@@ -62,8 +62,8 @@ def workload(name):
                     key="twolevel1d", mol=mol, model=model, n_iter=20, spectra=True)
     if name == "grid3d":
         mol = LI.rotor_molecule()
-        model = LI.grid3d_cloud()
-        return dict(name="3D regular grid 128^3, 12-level rotor (11 lines), 128 channels, "
+        model = LI.grid3d_cloud(N=n_root)
+        return dict(name=f"3D regular grid {n_root}^3, 12-level rotor (11 lines), 128 channels, "
                          "48 HEALPix directions, 1 ALI iteration",
                     key="grid3d", mol=mol, model=model, n_iter=1, spectra=False)
     raise SystemExit(f"unknown workload {name}")
@@ -354,11 +354,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rotor1d", choices=["rotor1d", "twolevel1d", "grid3d"])
+    ap.add_argument("--n-root", type=int, default=128, help="grid3d: cells per side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.n_root)
     if args.impl == "reference":
         run_reference(args, wl)
     else:
