@@ -220,10 +220,13 @@ def run_gpu(args, wl):
     R = model["radius"][-1] if is1d else None
     p_spec = np.concatenate([[0.0], (np.arange(model["n_rays"]) + 0.5) * R / model["n_rays"]]) if is1d else None
     opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW)
+    tune_opts = dict(window_sigmas=WINDOW)
 
     m = loc.Model(model, mol)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    tuned_per, tuned_ms = m.autotune(**tune_opts)
 
     def step(profile=False):
         m.reset()
@@ -330,6 +333,7 @@ def run_gpu(args, wl):
                 "config": {"workload": wl["name"], "iterations_per_step": iters,
                            "ray_steps_per_iteration": seg, "channels": nch, "lines": T,
                            "window_sigmas": WINDOW, "models_per_step": world,
+                           "lines_per_warp": tuned_per,
                            "parallelism": f"replicas x{world}" if world > 1 else "single",
                            "l2": "flushed (256 MB write) between timed steps"},
                 "computed_updates_per_s": comp * world / (ms_total / 1e3),

@@ -67,8 +67,8 @@ typedef struct loc_allocator {
  *  radius       1D: [K] outer radii, strictly increasing, > 0.
  *  n_rays       1D: number of equidistant impact parameters
  *               p_j = (j + 1/2) R / n_rays (0 -> n_shells).
- *  n_root, h0   3D: N^3 root cells of size h0 (cm); cells are indexed
- *               x fastest: idx = (iz N + iy) N + ix.
+ *  n_root, h0   3D: N^3 root cells of size h0 (cm), 1 <= N <= 255; cells
+ *               are indexed x fastest: idx = (iz N + iy) N + ix.
  *  n_dir, dirs  3D: [n_dir][3] unit ray directions (e.g. HEALPix centres).
  *  octree_levels, octree_refine, octree_n_cells
  *               octree: number of levels below the root, and per cell a
@@ -205,6 +205,15 @@ loc_status loc_reset_populations(loc_model *m);
  * equilibrium solve: fills the per-cell accumulators read by
  * loc_get_radiation (for step-by-step checks). */
 loc_status loc_march(loc_model *m, const loc_iter_opts *o);
+
+/* Choose the number of lines each warp carries through the march (the
+ * launch shape: more lines per warp share the profile and the walk, fewer
+ * give more warps and fewer registers per thread) by timing one ray
+ * simulation per candidate with CUDA events on the model's stream; the
+ * fastest is used by later calls whose lines_per_pass is 0.  Runs ray
+ * simulations with the current populations (overwrites the accumulators).
+ * best_per / best_ms (may be NULL) receive the choice and its time. */
+loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, double *best_ms);
 
 /* Per-cell accumulators of the last ray simulation, as FP64:
  * sij, esc [n_lines][n_cells] and norm [n_cells] (any may be NULL).

@@ -1,0 +1,221 @@
+// k_march.cuh -- the ray march: one radiation-field simulation (Sect. 2).
+//
+// For every ray and velocity channel the march crosses the cells in order
+// and, per step of length s through cell c, evaluates the channel-integrated
+// Gaussian profile phi_k Doppler-shifted by the line-of-sight velocity at the
+// step's start, the optical depth tau_k = K phi_k s, and
+//   SIJ_c += w sum_k phi_k I_k f_k,   ESC_c += w sum_k phi_k f_k,
+//   NORM_c += w sum_k phi_k,          I_k <- I_k e^-tau_k + S (1 - e^-tau_k),
+// with f = (1 - e^-tau) / tau (the external term of Eq. 2 and, through ESC,
+// the local term that ALI removes; Eq. 3 for the update).  Since
+// phi_k f_k = (1 - e^-tau_k) / (K s), the per-channel sums only need
+// t_k = 1 - e^-tau_k and one division per (step, line).
+//
+// GB300 mapping: one warp per ray (and group of at most 15 lines), lanes
+// over channels, the ray's intensities I[line][channel] in shared memory,
+// the profile computed once per step and channel and reused by every line
+// of the group, channels optionally restricted to a window around the local
+// line centre (Sect. A.2).  The per-step sums {SIJ_t, ESC_t, NORM} of all
+// lanes are combined by a transpose-reduction that leaves line t's totals
+// in lane t, so each step ends with one coalesced vector atomic {SIJ, ESC}
+// per line into the cell's contiguous [cell][line] record.  The next step's
+// cell data is loaded while the current step computes.
+#pragma once
+
+#include "loc_internal.cuh"
+#include "walk3d.cuh"
+
+namespace loc {
+
+constexpr int kWarpsPerBlock = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Channel fraction of a Gaussian between b0 and b0 + db (arguments in units
+// of sqrt(2) sigma), written with upper tails so both wings keep relative
+// accuracy.
+__device__ __forceinline__ float chan_phi(float b0, float db)
+{
+    const float b1 = b0 + db;
+    const float e0 = 0.5f * erfcf(fabsf(b0));
+    const float e1 = 0.5f * erfcf(fabsf(b1));
+    return (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
+}
+
+// 1 - e^-tau: series for |tau| < 1/8 (truncation < 1e-9 relative), the
+// exponential otherwise; both evaluated, no divergence.
+__device__ __forceinline__ float one_minus_exp(float tau)
+{
+    float p = 1.f - tau * (1.f / 6.f);
+    p = 1.f - tau * (1.f / 5.f) * p;
+    p = 1.f - tau * (1.f / 4.f) * p;
+    p = 1.f - tau * (1.f / 3.f) * p;
+    p = 1.f - tau * 0.5f * p;
+    const float e = __expf(-tau);
+    return (fabsf(tau) < 0.125f) ? tau * p : 1.f - e;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+// Sum of v[i] over the 32 lanes for all i at once; lane l receives the
+// total of index l (recursive halving: 31 shuffles for 32 values).
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < m; i++) {
+            const float send = up ? v[i] : v[i + m];
+            const float keep = up ? v[i + m] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, m);
+        }
+    }
+    return v[0];
+}
+
+// Data of one ray step.
+template <int G>
+struct Step {
+    long long cell;
+    float s, w;          // path length (cm), weight of the step
+    float vlos, inv;     // line-of-sight velocity, 1/(sqrt(2) sigma)
+    float2 ks[G];        // {K, S} of the lines of this pass
+};
+
+template <int G>
+__device__ __forceinline__ void load_lines(const DevModel &m, const MarchArgs &a, Step<G> &st)
+{
+    const float2 *p = m.ks + st.cell * m.T + a.line0;
+#pragma unroll
+    for (int t = 0; t < G; t++) st.ks[t] = (t < a.n_lines) ? p[t] : make_float2(0.f, 0.f);
+}
+
+// Process one step.  All lanes call it with identical arguments.  Returns
+// the number of channels computed.
+template <int G>
+__device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
+                                          const Step<G> &st, int lane)
+{
+    const int nch = m.n_ch;
+    const float dv = (float)m.dv;
+    const float u0 = ((float)m.v_min + st.vlos) / dv;   // channel coordinate offset
+    const float db = dv * st.inv;                        // channel width in b units
+    int klo = 0, khi = nch;
+    if (a.window > 0.f) {
+        const float hw = a.window / (1.41421356f * db);  // window half-width, channels
+        const float cen = -u0;
+        klo = (int)fminf(fmaxf(floorf(cen - hw), 0.f), (float)nch);
+        khi = (int)fminf(fmaxf(ceilf(cen + hw), 0.f), (float)nch);
+    }
+    float Ks[G], sij[G], esc[G];
+#pragma unroll
+    for (int t = 0; t < G; t++) {
+        float k = st.ks[t].x * st.s;
+        // keep |K s| >= 1e-20 so that (1 - e^-tau) / (K s) stays phi
+        if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
+        Ks[t] = k;
+        sij[t] = 0.f;
+        esc[t] = 0.f;
+    }
+    // channels in chunks of 31: lane l evaluates the Gaussian tail at the
+    // lower edge of channel base + l and takes the upper edge from lane l + 1
+    float nrm = 0.f;
+    for (int base = klo; base < khi; base += 31) {
+        const int k = base + lane;
+        const float b0 = ((float)k + u0) * db;
+        const float e0 = 0.5f * erfcf(fabsf(b0));
+        const float b1 = __shfl_down_sync(kFull, b0, 1);
+        const float e1 = __shfl_down_sync(kFull, e0, 1);
+        if (lane < 31 && k < khi) {
+            const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
+            nrm += phi;
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                if (t < a.n_lines) {
+                    const float tm = one_minus_exp(Ks[t] * phi);
+                    float *ip = I + t * nch + k;
+                    const float iv = *ip;
+                    sij[t] = fmaf(iv, tm, sij[t]);
+                    esc[t] += tm;
+                    *ip = fmaf(st.ks[t].y - iv, tm, iv);
+                }
+            }
+        }
+    }
+    // lane t < n_lines ends with line t's {SIJ, ESC}; lane 15 with NORM
+    float my_sij, my_esc, my_nrm;
+    if (G <= 2) {
+        my_sij = 0.f;
+        my_esc = 0.f;
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            const float a1 = warp_sum(sij[t]), a2 = warp_sum(esc[t]);
+            if (lane == t) { my_sij = a1; my_esc = a2; }
+        }
+        my_nrm = a.do_norm ? warp_sum(nrm) : 0.f;
+    } else {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = 0.f;
+#pragma unroll
+        for (int t = 0; t < G; t++) { v[t] = sij[t]; v[16 + t] = esc[t]; }
+        v[15] = nrm;
+        const float r = transpose_reduce32(v, lane);
+        my_sij = r;
+        my_esc = __shfl_down_sync(kFull, r, 16);
+        my_nrm = r;   // meaningful in lane 15
+    }
+    if (a.do_norm && lane == 15) {
+        if (a.fp64_acc) atomicAdd(m.norm64 + st.cell, (double)st.w * (double)my_nrm);
+        else atomicAdd(m.norm + st.cell, st.w * my_nrm);
+    }
+    if (lane < a.n_lines) {
+        float my_ks = 1.f;
+#pragma unroll
+        for (int t = 0; t < G; t++) if (lane == t) my_ks = Ks[t];
+        const long long o = st.cell * m.T + a.line0 + lane;
+        if (a.fp64_acc) {
+            const double f = (double)st.w / (double)my_ks;
+            atomicAdd(m.acc64 + 2 * o, f * (double)my_sij);
+            atomicAdd(m.acc64 + 2 * o + 1, f * (double)my_esc);
+        } else {
+            const float f = __fdividef(st.w, my_ks);
+            atomicAdd(m.acc + o, make_float2(my_sij * f, my_esc * f));
+        }
+    }
+    return khi - klo;
+}
+
+template <int G>
+__device__ __forceinline__ void init_ray(const DevModel &m, const MarchArgs &a, float *I, int lane)
+{
+    for (int t = 0; t < a.n_lines; t++) {
+        const float nb = m.nbg[a.line0 + t];
+        for (int k = lane; k < m.n_ch; k += 32) I[t * m.n_ch + k] = nb;
+    }
+    __syncwarp();
+}
+
+// add this warp's computed-update count (profiling)
+__device__ __forceinline__ void flush_count(const DevModel &m, const MarchArgs &a, long long nw,
+                                            int lane)
+{
+    if (a.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)(nw * a.n_lines));
+}
+
+// The work item of a warp is (ray, line group); the group fixes line0 and
+// n_lines, and group 0 also accumulates NORM.
+__device__ __forceinline__ MarchArgs warp_args(const DevModel &m, MarchArgs a, int g)
+{
+    a.line0 = g * a.per;
+    a.n_lines = min(a.per, m.T - a.line0);
+    a.do_norm = (g == 0);
+    return a;
+}
+
+}  // namespace loc

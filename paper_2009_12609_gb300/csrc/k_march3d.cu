@@ -1,0 +1,99 @@
+// k_march3d.cu -- ray march over a regular 3D grid (Sect. 2.2); the walk is
+// GridWalk in walk3d.cuh, the per-step update march_step in k_march.cuh.
+#include "k_march.cuh"
+
+namespace loc {
+
+// 3D regular grid: one warp per (direction, root line, line group).
+template <int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m, MarchArgs a0)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const long long item0 = (long long)blockIdx.x * kWarpsPerBlock + wid;
+    const long long per_dir = (long long)m.N * m.N;
+    if (item0 >= per_dir * m.n_dir * a0.n_groups) return;
+    const long long item = item0 / a0.n_groups;
+    const MarchArgs a = warp_args(m, a0, (int)(item0 - item * a0.n_groups));
+    const int dir = (int)(item / per_dir);
+    const long long r = item - (long long)dir * per_dir;
+    const long long i = r / m.N, j = r - (r / m.N) * m.N;
+    float *I = smem + (size_t)wid * a.per * m.n_ch;
+    init_ray<G>(m, a, I, lane);
+    const Dir3D D = m.dirs[dir];
+    const float wscale = 1.0f / ((float)(1ll << kFixedBits) * (float)m.n_dir);
+    GridWalk wk;
+    wk.init(D, i, j);
+    auto fetch = [&](Step<G> &st) {
+        long long dz;
+        wk.step(D, m.N, st.cell, dz);
+        const float4 cv = m.vel[st.cell];
+        st.vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
+        st.inv = cv.w;
+        st.s = (float)dz * D.unit;
+        st.w = (float)dz * wscale;
+        load_lines<G>(m, a, st);
+    };
+    long long nw = 0;
+    Step<G> cur, nxt;
+    fetch(cur);
+    while (true) {
+        const bool more = !wk.done(m.N);
+        if (more) fetch(nxt);
+        nw += march_step<G>(m, a, I, cur, lane);
+        __syncwarp();
+        if (!more) break;
+        cur = nxt;
+    }
+    flush_count(m, a, nw, lane);
+}
+
+
+template <int G>
+static loc_status launch_g(const DevModel &m, const MarchArgs &a, cudaStream_t st)
+{
+    const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+    const long long items = (long long)m.N * m.N * m.n_dir * a.n_groups;
+    const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    LOC_CUDA_TRY(cudaFuncSetAttribute(march3d_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    march3d_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st)
+{
+    switch (a.per) {
+    case 1: return launch_g<1>(m, a, st);
+    case 2: return launch_g<2>(m, a, st);
+    case 3: return launch_g<3>(m, a, st);
+    case 4: return launch_g<4>(m, a, st);
+    case 5: return launch_g<5>(m, a, st);
+    case 6: return launch_g<6>(m, a, st);
+    case 7: return launch_g<7>(m, a, st);
+    case 8: return launch_g<8>(m, a, st);
+    case 9: return launch_g<9>(m, a, st);
+    case 10: return launch_g<10>(m, a, st);
+    case 11: return launch_g<11>(m, a, st);
+    case 12: return launch_g<12>(m, a, st);
+    case 13: return launch_g<13>(m, a, st);
+    case 14: return launch_g<14>(m, a, st);
+    default: return launch_g<15>(m, a, st);
+    }
+}
+
+loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st)
+{
+    const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+    if (smem > 227 * 1024 || a.per > kMaxLinesPerWarp || a.per < 1 ||
+        a.n_groups != (m.T + a.per - 1) / a.per) {
+        set_error("march: %d lines per warp x %d channels need %zu B of shared memory per block",
+                  a.per, m.n_ch, smem);
+        return LOC_EINVAL;
+    }
+    if (m.geometry == LOC_SHELLS_1D) return launch_march1d(m, a, st);
+    return launch_march3d(m, a, st);
+}
+
+}  // namespace loc

@@ -18,7 +18,7 @@
 // C_ul = n_H2 k_ul, C_lu = C_ul (g_u / g_l) exp(-(E_u - E_l) / T_kin).  The
 // first balance equation is replaced by sum(x) = 1 and the system is solved
 // in FP64 by Gaussian elimination with partial pivoting, one cell per
-// thread.  The same kernel reports max |dT_ex| / |T_ex| over cells and lines
+// warp.  The same kernel reports max |dT_ex| / |T_ex| over cells and lines
 // whose upper level holds at least 1e-6 of the molecules.
 #include "loc_internal.cuh"
 
@@ -101,8 +101,10 @@ __device__ __forceinline__ double tex_of(const DevModel &m, int t, const double 
     return (kH * m.line_nu[t] / kKB) / log(m.g[u] * xl / (m.g[l] * xu));
 }
 
+// One thread per cell (large models: enough cells to fill the GPU, FP64
+// throughput is the limit).  Same rate assembly order as the warp version.
 template <int LMAX>
-__global__ void __launch_bounds__(128) se_kernel(DevModel m, int ali, int fp64_acc)
+__global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int fp64_acc)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float my_d = 0.f;
@@ -111,40 +113,38 @@ __global__ void __launch_bounds__(128) se_kernel(DevModel m, int ali, int fp64_a
         double M[LMAX][LMAX + 1];
         for (int i = 0; i < L; i++)
             for (int j = 0; j <= L; j++) M[i][j] = 0.0;
-        // norm
-        double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
+        const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
         for (int t = 0; t < m.T; t++) {
             const int u = m.line_u[t], l = m.line_l[t];
             const double A = m.line_A[t];
             const long long o = c * m.T + t;
             double J, beta;
             if (nrm > 0.0) {
-                double s, e;
-                if (fp64_acc) { s = m.acc64[2 * o]; e = m.acc64[2 * o + 1]; }
-                else { const float2 a = m.acc[o]; s = a.x; e = a.y; }
-                J = s / nrm;
-                beta = e / nrm;
+                double sj, ej;
+                if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
+                else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
+                J = sj / nrm;
+                beta = ej / nrm;
             } else {
                 J = m.nbg64[t];
                 beta = 1.0;
             }
             if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
-            const double rul = A * (beta + J);
-            const double rlu = (m.g[u] / m.g[l]) * A * J;
-            M[l][u] += rul; M[u][u] -= rul;
-            M[u][l] += rlu; M[l][l] -= rlu;
+            const double rd = A * (beta + J);
+            const double ru = (m.g[u] / m.g[l]) * A * J;
+            M[l][u] += rd; M[l][l] -= ru;
+            M[u][u] -= rd; M[u][l] += ru;
         }
-        const double T = m.t_kin[c], nh = m.n_h2[c];
+        const double Tk = m.t_kin[c], nh = m.n_h2[c];
         for (int p = 0; p < m.P; p++) {
             const int u = m.coll_u[p], l = m.coll_l[p];
-            const double cul = nh * m.coll_k[p];
-            const double clu = cul * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / T);
-            M[l][u] += cul; M[u][u] -= cul;
-            M[u][l] += clu; M[l][l] -= clu;
+            const double rd = nh * m.coll_k[p];
+            const double ru = rd * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / Tk);
+            M[l][u] += rd; M[l][l] -= ru;
+            M[u][u] -= rd; M[u][l] += ru;
         }
         for (int j = 0; j < L; j++) M[0][j] = 1.0;
         M[0][L] = 1.0;
-        // Gaussian elimination with partial pivoting (augmented column L)
         for (int p = 0; p < L; p++) {
             int piv = p;
             double best = fabs(M[p][p]);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) se_kernel(DevModel m, int ali, int fp64_a
             for (int j = i + 1; j < L; j++) a -= M[i][j] * xs[j];
             xs[i] = a / M[i][i];
         }
-        double *xo = m.x + c * L;
+        const double *xo = m.x + c * L;
         double *xn = m.x_new + c * L;
         for (int i = 0; i < L; i++) xn[i] = xs[i];
         for (int t = 0; t < m.T; t++) {
@@ -173,31 +173,164 @@ __global__ void __launch_bounds__(128) se_kernel(DevModel m, int ali, int fp64_a
             const double a = tex_of(m, t, xo);
             if (a == 0.0) continue;
             const double b = tex_of(m, t, xs);
-            const float d = (float)(fabs(b - a) / fabs(a));
-            my_d = fmaxf(my_d, d);
+            my_d = fmaxf(my_d, (float)(fabs(b - a) / fabs(a)));
         }
     }
-    // block max -> one atomic (non-negative floats order like their bits)
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) my_d = fmaxf(my_d, __shfl_xor_sync(0xffffffffu, my_d, off));
-    __shared__ float wmax[4];
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = my_d;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float v = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v = fmaxf(v, wmax[w]);
-        if (v > 0.f) atomicMax(m.dtex_bits, __float_as_uint(v));
+    if ((threadIdx.x & 31) == 0 && my_d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(my_d));
+}
+
+// One warp per cell.  Lanes compute the radiative and collisional rates of
+// the lines and pairs (k, k+32, ...) into shared memory; lane i then adds
+// the rates that touch level i into row i of the matrix in a fixed order
+// (deterministic); elimination runs with lanes over columns, back
+// substitution with one warp sum per row.
+constexpr int kSeWarps = 4;
+// at or above this many cells one thread per cell already fills the GPU
+constexpr long long kSeThreadCells = 1ll << 16;
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(kSeWarps * 32) se_kernel(DevModel m, int ali, int fp64_acc)
+{
+    constexpr int W = LMAX + 2;                     // row stride: L columns + rhs + pad
+    extern __shared__ double se_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nrate = m.T + m.P;
+    double *M = se_smem + (size_t)wid * (LMAX * W + LMAX + 2 * nrate);
+    double *F = M + LMAX * W;                       // factors, then the solution
+    double *R = F + LMAX;                           // [nrate][2] downward / upward rates
+    const long long c = (long long)blockIdx.x * kSeWarps + wid;
+    float my_d = 0.f;
+    if (c < m.n_cells) {
+        const int L = m.L;
+        const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
+        for (int t = lane; t < m.T; t += 32) {
+            const int u = m.line_u[t], l = m.line_l[t];
+            const double A = m.line_A[t];
+            const long long o = c * m.T + t;
+            double J, beta;
+            if (nrm > 0.0) {
+                double sj, ej;
+                if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
+                else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
+                J = sj / nrm;
+                beta = ej / nrm;
+            } else {
+                J = m.nbg64[t];
+                beta = 1.0;
+            }
+            if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
+            R[2 * t] = A * (beta + J);                          // u -> l
+            R[2 * t + 1] = (m.g[u] / m.g[l]) * A * J;           // l -> u
+        }
+        const double Tk = m.t_kin[c], nh = m.n_h2[c];
+        for (int p = lane; p < m.P; p += 32) {
+            const int u = m.coll_u[p], l = m.coll_l[p];
+            const double cul = nh * m.coll_k[p];
+            R[2 * (m.T + p)] = cul;
+            R[2 * (m.T + p) + 1] = cul * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / Tk);
+        }
+        for (int i = lane; i < L * W; i += 32) M[i] = 0.0;
+        __syncwarp();
+        // balance of level i: sum_j x_j R(j -> i) - x_i sum_j R(i -> j) = 0
+        if (lane < L) {
+            double *row = M + lane * W;
+            for (int q = 0; q < nrate; q++) {
+                int u, l;
+                if (q < m.T) { u = m.line_u[q]; l = m.line_l[q]; }
+                else { u = m.coll_u[q - m.T]; l = m.coll_l[q - m.T]; }
+                const double rd = R[2 * q], ru = R[2 * q + 1];
+                if (lane == l) { row[u] += rd; row[l] -= ru; }
+                if (lane == u) { row[u] -= rd; row[l] += ru; }
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j <= L; j += 32) M[j] = 1.0;         // row 0: sum(x) = 1
+        __syncwarp();
+        for (int p = 0; p < L; p++) {
+            // pivot: the first row i >= p with the largest |M[i][p]|
+            double v = (lane >= p && lane < L) ? fabs(M[lane * W + p]) : -1.0;
+            int idx = lane;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+            }
+            if (idx != p) {
+                for (int j = lane; j <= L; j += 32) {
+                    const double tmp = M[p * W + j];
+                    M[p * W + j] = M[idx * W + j];
+                    M[idx * W + j] = tmp;
+                }
+            }
+            __syncwarp();
+            const double inv = 1.0 / M[p * W + p];
+            if (lane > p && lane < L) F[lane] = M[lane * W + p] * inv;
+            __syncwarp();
+            for (int j = p + lane; j <= L; j += 32) {
+                const double pj = M[p * W + j];
+                for (int i = p + 1; i < L; i++) M[i * W + j] -= F[i] * pj;
+            }
+            __syncwarp();
+        }
+        double xi = 0.0;
+        for (int i = L - 1; i >= 0; i--) {
+            const double part = warp_sum_d((lane > i && lane < L) ? M[i * W + lane] * xi : 0.0);
+            const double xv = (M[i * W + L] - part) / M[i * W + i];
+            if (lane == i) xi = xv;
+        }
+        __syncwarp();
+        if (lane < L) {
+            m.x_new[c * L + lane] = xi;
+            F[lane] = xi;
+        }
+        __syncwarp();
+        const double *xo = m.x + c * L;
+        for (int t = lane; t < m.T; t += 32) {
+            if (F[m.line_u[t]] < 1e-6) continue;
+            const double a = tex_of(m, t, xo);
+            if (a == 0.0) continue;
+            const double b = tex_of(m, t, F);
+            my_d = fmaxf(my_d, (float)(fabs(b - a) / fabs(a)));
+        }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) my_d = fmaxf(my_d, __shfl_xor_sync(0xffffffffu, my_d, off));
+    if (lane == 0 && my_d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(my_d));
+}
+
+template <int LMAX>
+static loc_status launch_se_l(const DevModel &m, int ali, int fp64_acc, cudaStream_t st)
+{
+    if (m.n_cells >= kSeThreadCells) {
+        const unsigned nbt = (unsigned)((m.n_cells + 127) / 128);
+        se_thread_kernel<LMAX><<<nbt, 128, 0, st>>>(m, ali, fp64_acc);
+        LOC_CUDA_TRY(cudaGetLastError());
+        return LOC_OK;
+    }
+    const size_t smem = sizeof(double) * kSeWarps * (LMAX * (LMAX + 2) + LMAX + 2 * (m.T + m.P));
+    LOC_CUDA_TRY(cudaFuncSetAttribute(se_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned nb = (unsigned)((m.n_cells + kSeWarps - 1) / kSeWarps);
+    se_kernel<LMAX><<<nb, kSeWarps * 32, smem, st>>>(m, ali, fp64_acc);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
 }
 
 loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((m.n_cells + 127) / 128);
-    if (m.L <= 4) se_kernel<4><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
-    else if (m.L <= 8) se_kernel<8><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
-    else if (m.L <= 16) se_kernel<16><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
-    else se_kernel<32><<<nb, 128, 0, st>>>(m, ali, fp64_acc);
-    LOC_CUDA_TRY(cudaGetLastError());
-    return LOC_OK;
+    if (m.L <= 4) return launch_se_l<4>(m, ali, fp64_acc, st);
+    if (m.L <= 8) return launch_se_l<8>(m, ali, fp64_acc, st);
+    if (m.L <= 16) return launch_se_l<16>(m, ali, fp64_acc, st);
+    return launch_se_l<32>(m, ali, fp64_acc, st);
 }
 
 __global__ void tex_kernel(DevModel m, int t, double *out)

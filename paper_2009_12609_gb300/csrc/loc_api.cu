@@ -41,6 +41,7 @@ struct loc_model {
     int last_fp64 = 0;
     long long segs_per_sim = 0;
     int n_sm = 152;
+    int tuned_per = 0;               // lines per warp chosen by loc_autotune (0: heuristic)
 };
 
 static void *dev_alloc(loc_model *m, size_t bytes, std::vector<void *> &owner)
@@ -140,7 +141,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         D.n_rays = d->n_rays > 0 ? d->n_rays : K;
         CHECK(D.n_rays <= (1 << 16), "n_rays must be <= 65536");
     } else if (d->geometry == LOC_GRID_3D) {
-        CHECK(d->n_root >= 1 && d->n_root <= 1024, "n_root must be in [1, 1024]");
+        CHECK(d->n_root >= 1 && d->n_root <= 255, "n_root must be in [1, 255]");
         CHECK(d->h0 > 0.0 && std::isfinite(d->h0), "h0 must be > 0");
         CHECK(d->n_dir >= 1 && d->dirs, "3D model needs directions");
         for (int i = 0; i < d->n_dir; i++) {
@@ -344,6 +345,7 @@ static loc_status check_opts(const loc_iter_opts *o)
 static int lines_per_warp(const loc_model *m, const loc_iter_opts *o)
 {
     const DevModel &D = m->d;
+    if (o->lines_per_pass == 0 && m->tuned_per > 0 && m->tuned_per <= D.T) return m->tuned_per;
     int per = o->lines_per_pass > 0 ? o->lines_per_pass : D.T;
     if (per > kMaxLinesPerWarp) per = kMaxLinesPerWarp;
     if (per > D.T) per = D.T;
@@ -381,6 +383,56 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
     TRY(launch_march(D, a, m->st));
     m->has_rad = true;
     m->last_fp64 = fp64;
+    return LOC_OK;
+}
+
+loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, double *best_ms)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    TRY(check_opts(o));
+    if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
+    const DevModel &D = m->d;
+    m->tuned_per = 0;
+    std::vector<int> cand;
+    for (int parts = 1; parts <= D.T; parts++) {
+        int per = (D.T + parts - 1) / parts;
+        if (per > kMaxLinesPerWarp) continue;
+        if (4ll * per * D.n_ch * 4 > 200 * 1024) continue;
+        bool seen = false;
+        for (int c : cand) seen |= (c == per);
+        if (!seen) cand.push_back(per);
+        if (cand.size() >= 6) break;
+    }
+    if (cand.empty()) cand.push_back(1);
+    TRY(launch_line_params(m->d, m->st));
+    cudaEvent_t e0, e1;
+    LOC_CUDA_TRY(cudaEventCreate(&e0));
+    LOC_CUDA_TRY(cudaEventCreate(&e1));
+    int best = cand[0];
+    float best_t = 1e30f;
+    loc_iter_opts oo = *o;
+    loc_status st = LOC_OK;
+    for (int per : cand) {
+        oo.lines_per_pass = per;
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 2 && st == LOC_OK; rep++) {
+            cudaEventRecord(e0, m->st);
+            st = march_impl(m, &oo);
+            cudaEventRecord(e1, m->st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { set_error("autotune march failed"); st = LOC_ECUDA; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < t_min) t_min = ms;
+        }
+        if (st != LOC_OK) break;
+        if (t_min < best_t) { best_t = t_min; best = per; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LOC_OK) return st;
+    m->tuned_per = best;
+    if (best_per) *best_per = best;
+    if (best_ms) *best_ms = best_t;
     return LOC_OK;
 }
 

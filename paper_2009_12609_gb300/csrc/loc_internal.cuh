@@ -126,6 +126,8 @@ loc_status launch_geom1d(const DevModel &m, cudaStream_t st);
 loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W);
 loc_status launch_line_params(const DevModel &m, cudaStream_t st);
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
+loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
+loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);
 loc_status launch_lte(const DevModel &m, cudaStream_t st);
 loc_status launch_bg(const DevModel &m, cudaStream_t st);

@@ -18,8 +18,18 @@
 
 namespace loc {
 
+// z, the crossings and the main-axis boundary fit in 32 bits for grids of up
+// to 255 root cells per side (255 x 2^24 < 2^32); the quotient / remainder
+// state stays 64-bit and is only touched when a crossing happens.
+constexpr unsigned kNever = 0xffffffffu;
+
+__device__ __forceinline__ unsigned sat32(long long v)
+{
+    return (v >= (long long)kNever) ? kNever : (unsigned)v;
+}
+
 struct GridWalk {
-    long long z, za, zb;        // current z, next a / b crossing
+    unsigned z, za, zb;         // current z, next a / b crossing
     long long Qa, Ra, Qb, Rb;   // quotient / remainder of the current targets
     int ia, ib, im;             // (mirrored) cell indices along a, b, main
 
@@ -31,20 +41,20 @@ struct GridWalk {
         im = 0;
         Qa = D.Qa0; Ra = D.Ra0;
         Qb = D.Qb0; Rb = D.Rb0;
-        za = (D.qa > 0) ? Qa + (Ra > 0) : LLONG_MAX;
-        zb = (D.qb > 0) ? Qb + (Rb > 0) : LLONG_MAX;
+        za = (D.qa > 0) ? sat32(Qa + (Ra > 0)) : kNever;
+        zb = (D.qb > 0) ? sat32(Qb + (Rb > 0)) : kNever;
     }
 
     __device__ __forceinline__ bool done(int N) const
     {
-        return z >= ((long long)N << kFixedBits);
+        return z >= ((unsigned)N << kFixedBits);
     }
 
     // Current segment's cell (x fastest) and length; advances the walk.
     __device__ __forceinline__ void step(const Dir3D &D, int N, long long &cell, long long &dz)
     {
-        const long long zm = (long long)(im + 1) << kFixedBits;
-        long long zn = zm;
+        const unsigned zm = (unsigned)(im + 1) << kFixedBits;
+        unsigned zn = zm;
         if (za < zn) zn = za;
         if (zb < zn) zn = zb;
         int idx[3];
@@ -55,20 +65,20 @@ struct GridWalk {
         const int iy = D.flip[1] ? N - 1 - idx[1] : idx[1];
         const int iz = D.flip[2] ? N - 1 - idx[2] : idx[2];
         cell = ((long long)iz * N + iy) * N + ix;
-        dz = zn - z;
+        dz = (long long)(zn - z);
         z = zn;
         if (z == zm) im++;
         if (z == za) {
             ia = (ia + 1 == N) ? 0 : ia + 1;
             Qa += D.Da; Ra += D.ra;
             if (Ra >= D.qa) { Ra -= D.qa; Qa++; }
-            za = Qa + (Ra > 0);
+            za = sat32(Qa + (Ra > 0));
         }
         if (z == zb) {
             ib = (ib + 1 == N) ? 0 : ib + 1;
             Qb += D.Db; Rb += D.rb;
             if (Rb >= D.qb) { Rb -= D.qb; Qb++; }
-            zb = Qb + (Rb > 0);
+            zb = sat32(Qb + (Rb > 0));
         }
     }
 };

@@ -95,7 +95,7 @@ EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecul
            "loc_iterate", "loc_march", "loc_get_radiation", "loc_get_populations",
            "loc_set_populations", "loc_get_tex", "loc_spectra", "loc_model_info",
            "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
-           "loc_radiation1d_noalloc"]
+           "loc_radiation1d_noalloc", "loc_autotune"]
 
 
 def library_path():
@@ -119,6 +119,8 @@ def load():
     lib.loc_iterate.argtypes = [_vp, ctypes.POINTER(loc_iter_opts), ctypes.POINTER(loc_iter_report)]
     lib.loc_march.argtypes = [_vp, ctypes.POINTER(loc_iter_opts)]
     lib.loc_reset_populations.argtypes = [_vp]
+    lib.loc_autotune.argtypes = [_vp, ctypes.POINTER(loc_iter_opts), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double)]
     lib.loc_get_radiation.argtypes = [_vp, _d, _d, _d, ctypes.c_size_t, ctypes.c_size_t]
     lib.loc_get_populations.argtypes = [_vp, _d, ctypes.c_size_t]
     lib.loc_set_populations.argtypes = [_vp, _d, ctypes.c_size_t]
@@ -300,6 +302,14 @@ def loc_iterate(h, **opts):
                 computed_updates=r.computed_updates)
 
 
+def loc_autotune(h, **opts):
+    per = ctypes.c_int()
+    ms = ctypes.c_double()
+    o = iter_opts(**opts)
+    _check(load().loc_autotune(h, ctypes.byref(o), ctypes.byref(per), ctypes.byref(ms)))
+    return per.value, ms.value
+
+
 def loc_reset_populations(h):
     _check(load().loc_reset_populations(h))
 
@@ -398,6 +408,9 @@ class Model:
 
     def reset(self):
         loc_reset_populations(self.h)
+
+    def autotune(self, **opts):
+        return loc_autotune(self.h, **opts)
 
     def march(self, **opts):
         loc_march(self.h, **opts)

@@ -122,3 +122,21 @@ def test_full_size_isothermal_invariant(loc):
     S = nbg[:, None]
     Jbar = (sij + S * (norm - esc)) / norm
     np.testing.assert_allclose(Jbar / S, 1.0, rtol=3e-5)
+
+
+def test_autotune_choice_keeps_parity(loc, oracle):
+    """The autotuner only changes the launch shape (lines per warp): the
+    accumulators must stay within the parity tolerance for its choice."""
+    mol = LI.rotor_molecule(n_levels=10)
+    g = LI.small_grid3d(N=6, n_ch=40, nside=2)
+    with loc.Model(g, mol) as m:
+        per, ms = m.autotune(window_sigmas=8.0)
+        assert 1 <= per <= 9 and ms > 0
+        m.march(window_sigmas=8.0)
+        sij, esc, norm = m.radiation()
+    x = oracle.lte_populations(mol, g["t_kin"])
+    Kp, S = oracle.line_params(mol, g, x)
+    rs, re_, rn = oracle.march_grid3d(mol, g, Kp, S)
+    np.testing.assert_allclose(norm, rn, rtol=2e-5)
+    np.testing.assert_allclose(sij, rs, rtol=2e-5, atol=1e-12 * np.abs(rs).max())
+    np.testing.assert_allclose(esc, re_, rtol=2e-5)
