@@ -351,18 +351,107 @@ def run_gpu(args, wl):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Continuous-batching server on the stream of seeded 1D requests:
+    closed loop (all submitted at once) for the saturated converged-models/s,
+    then Poisson arrivals at 0.8x that rate for p50/p99 latency; beside it the
+    plain path: the same requests solved one at a time with FP64 per-cell
+    accumulation."""
+    import torch
+    from paper_2009_12609_gb300 import build, loc
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    loc.load()
+    n = args.requests
+    tol, max_iter = 1e-4, 300
+    reqs = LI.serving_requests(n=n)
+    mols = {L: LI.rotor_molecule(n_levels=L) for L in range(2, 21)}
+    srv_opts = dict(max_slots=args.slots, mem_budget_bytes=args.mem_gb << 30,
+                    iters_per_launch=4, window_sigmas=WINDOW)
+    # warm-up (kernels loaded, graph captured, pool primed)
+    with loc.Server(**srv_opts) as srv:
+        ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=3) for r in reqs[:8]]
+        for t in ts:
+            srv.poll(t, 600000)
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    with loc.Server(**srv_opts) as srv:
+        t0 = time.perf_counter()
+        ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol) for r in reqs]
+        res = [srv.poll(t, 3600 * 1000)[0] for t in ts]
+        closed_s = time.perf_counter() - t0
+    clocks = clk.stop()
+    conv = sum(1 for r in res if r["status"] == 0)
+    upd = sum(r["updates"] for r in res)
+    models_per_s = n / closed_s
+    # open loop: Poisson arrivals at 0.8x the saturated rate
+    rate = 0.8 * models_per_s
+    n_open = min(n, args.open_requests)
+    arr = LI.serving_requests(n=n_open, rate_hz=rate)
+    with loc.Server(**srv_opts) as srv:
+        t0 = time.perf_counter()
+        ts = []
+        for r in arr:
+            dt = r["arrival_s"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ts.append(srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol))
+        lat = np.array([srv.poll(t, 3600 * 1000)[0]["latency_ms"] for t in ts])
+        st = srv.stats()
+    # plain per-model path with FP64 accumulation, on a bounded subset
+    n_base = min(n, args.baseline_requests)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs[:n_base]:
+        with loc.Model(r["model"], mols[r["n_levels"]]) as m:
+            m.iterate(max_iter=max_iter, tol_tex=tol, precision="fp64acc", window_sigmas=WINDOW)
+    torch.cuda.synchronize()
+    base_models_per_s = n_base / (time.perf_counter() - t0)
+    line = {"metric": "converged 1D models/s at 1e-4 T_ex", "value": models_per_s,
+            "unit": "models/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"serving stream: {n} seeded 1D requests, shells U(32..1024), "
+                                   "channels {64,128,256,512}, levels U(2..20), scales x[0.1,10]",
+                       "slots": args.slots, "iters_per_launch": 4, "window_sigmas": WINDOW,
+                       "tol_tex": tol, "max_iter": max_iter},
+            "converged": conv, "updates_per_s": upd / closed_s,
+            "latency_open_loop": {"rate_hz": rate, "requests": n_open,
+                                  "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99)),
+                                  "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"]},
+            "per_model_fp64acc_models_per_s": base_models_per_s,
+            "per_model_requests_timed": n_base,
+            "speedup_vs_per_model_fp64acc": models_per_s / base_models_per_s,
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rotor1d", choices=["rotor1d", "twolevel1d", "grid3d"])
+    ap.add_argument("--workload", default="rotor1d",
+                    choices=["rotor1d", "twolevel1d", "grid3d", "serve"])
+    ap.add_argument("--requests", type=int, default=512, help="serve: requests in the stream")
+    ap.add_argument("--open-requests", type=int, default=256, help="serve: open-loop requests")
+    ap.add_argument("--baseline-requests", type=int, default=32,
+                    help="serve: requests solved one at a time by the per-model FP64 path")
+    ap.add_argument("--slots", type=int, default=256, help="serve: resident models")
+    ap.add_argument("--mem-gb", type=int, default=64, help="serve: device memory budget")
     ap.add_argument("--n-root", type=int, default=128, help="grid3d: cells per side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serve workload has no CPU arm"}))
+            return
+        run_serve(args)
+        return
     wl = workload(args.workload, args.n_root)
     if args.impl == "reference":
         run_reference(args, wl)

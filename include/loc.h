@@ -286,6 +286,71 @@ loc_status loc_radiation1d_noalloc(int n_shells, int n_rays, const double *radiu
                                    const float *nbg, double window_sigmas, float *j_ext,
                                    float *beta, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching server for 1D models.
+ *
+ * Many independent spherical models (the inverse-problem workload of the
+ * paper's introduction) are solved to convergence together: a host thread
+ * admits submitted models into free slots while the device-memory budget
+ * allows, keeps their populations on the device, and runs their ALI
+ * iterations (Sect. 2) as one batch -- one persistent launch per step kind,
+ * work items ordered longest ray first, iters_per_launch iterations per
+ * captured CUDA graph.  Models that arrive while others run join at the
+ * next graph boundary; converged models leave and free their slot.
+ * Thread-safe: submit and poll may be called from any thread.
+ * ------------------------------------------------------------------------ */
+typedef struct loc_server loc_server;
+
+typedef struct loc_server_opts {
+    int max_slots;             /* models resident at once (1..65536)          */
+    size_t mem_budget_bytes;   /* device memory admitted models may use       */
+    int iters_per_launch;      /* ALI iterations per graph launch (1..64)     */
+    double window_sigmas;      /* channel window of the march (0 = all)       */
+    int device;                /* CUDA device index                           */
+    int max_queue;             /* pending requests before LOC_EBUSY (0: no cap) */
+} loc_server_opts;
+
+typedef struct loc_result {
+    uint64_t ticket;
+    loc_status status;         /* LOC_OK, or LOC_ENOTCONV if tol not reached  */
+    int iterations;
+    double max_rel_dtex;       /* convergence metric of the last iteration    */
+    double latency_ms;         /* submit -> result available                  */
+    int64_t n_cells;
+    int n_levels;
+    double updates;            /* (step, channel, line) updates performed     */
+} loc_result;
+
+typedef struct loc_server_counters {
+    int64_t submitted, completed, active, queued;
+    int64_t device_bytes_in_use;
+    double p50_ms, p99_ms, mean_ms;   /* latency of completed requests        */
+    double models_per_s;              /* completed / (last completion - first submit) */
+} loc_server_counters;
+
+/* Start a server (allocates its tables, stream and host thread). */
+loc_status loc_server_create(loc_server **out, const loc_server_opts *o);
+
+/* Queue one 1D model (geometry LOC_SHELLS_1D; allocator and stream fields
+ * ignored) with its molecule and iteration options (max_iter, tol_tex, ali;
+ * FP32 march).  The arrays are copied before return.  *ticket identifies
+ * the result.  LOC_EBUSY if max_queue requests are already waiting. */
+loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_molecule_desc *mol,
+                             const loc_iter_opts *o, uint64_t *ticket);
+
+/* Wait up to timeout_ms (0: do not wait) for a result.  On success fills
+ * *out, copies the populations [n_cells][n_levels] into `populations` (may be
+ * NULL; n_out checked) and releases the result.  LOC_ETIMEOUT if not done in
+ * time (the request keeps running). */
+loc_status loc_server_poll(loc_server *s, uint64_t ticket, int timeout_ms, loc_result *out,
+                           double *populations, size_t n_out);
+
+/* Counters and latency percentiles; returns the server's fatal status. */
+loc_status loc_server_stats(loc_server *s, loc_server_counters *st);
+
+/* Stop the server: running and queued requests are abandoned. */
+void loc_server_destroy(loc_server *s);
+
 /* Wait for all queued work of the model. */
 loc_status loc_sync(loc_model *m);
 

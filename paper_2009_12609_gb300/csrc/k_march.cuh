@@ -218,4 +218,41 @@ __device__ __forceinline__ MarchArgs warp_args(const DevModel &m, MarchArgs a, i
     return a;
 }
 
+
+// One 1D ray (equidistant ray j) through all its steps for the warp's line
+// group; step records are fetched 32 at a time (one coalesced load) and
+// broadcast by shuffle, the next step's line data is prefetched.  Returns the
+// number of channels computed.
+template <int G>
+__device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchArgs &a, float *I,
+                                                 int j, int lane)
+{
+    init_ray<G>(m, a, I, lane);
+    const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
+    if (n <= 0) return 0;
+    Seg1D rec = {0, 0.f, 0.f, 0.f};
+    // step q of the ray (0 <= q < n); a new block of 32 records every 32 steps
+    auto fetch = [&](int q, Step<G> &st) {
+        const int r = q & 31;
+        if (r == 0 && q + lane < n) rec = m.segs[s0 + q + lane];
+        st.cell = __shfl_sync(kFull, rec.cell, r);
+        st.s = __shfl_sync(kFull, rec.s, r);
+        st.vlos = __shfl_sync(kFull, rec.vlos, r);
+        st.w = __shfl_sync(kFull, rec.w, r);
+        st.inv = m.inv_s2sig[st.cell];
+        load_lines<G>(m, a, st);
+    };
+    long long nw = 0;
+    Step<G> cur, nxt;
+    fetch(0, cur);
+    for (int q = 0; q < n; q++) {
+        const bool more = q + 1 < n;
+        if (more) fetch(q + 1, nxt);
+        nw += march_step<G>(m, a, I, cur, lane);
+        __syncwarp();
+        if (more) cur = nxt;
+    }
+    return nw;
+}
+
 }  // namespace loc

@@ -15,34 +15,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m
     const int j = (int)(item / a0.n_groups);
     const MarchArgs a = warp_args(m, a0, (int)(item - (long long)j * a0.n_groups));
     float *I = smem + (size_t)wid * a.per * m.n_ch;
-    init_ray<G>(m, a, I, lane);
-    const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
-    if (n <= 0) return;
-    Seg1D rec = {0, 0.f, 0.f, 0.f};
-    // step q of the ray (0 <= q < n); a new block of 32 records every 32 steps
-    auto fetch = [&](int q, Step<G> &st) {
-        const int r = q & 31;
-        if (r == 0 && q + lane < n) rec = m.segs[s0 + q + lane];
-        st.cell = __shfl_sync(kFull, rec.cell, r);
-        st.s = __shfl_sync(kFull, rec.s, r);
-        st.vlos = __shfl_sync(kFull, rec.vlos, r);
-        st.w = __shfl_sync(kFull, rec.w, r);
-        st.inv = m.inv_s2sig[st.cell];
-        load_lines<G>(m, a, st);
-    };
-    long long nw = 0;
-    Step<G> cur, nxt;
-    fetch(0, cur);
-    for (int q = 0; q < n; q++) {
-        const bool more = q + 1 < n;
-        if (more) fetch(q + 1, nxt);
-        nw += march_step<G>(m, a, I, cur, lane);
-        __syncwarp();
-        if (more) cur = nxt;
-    }
+    const long long nw = march_ray1d<G>(m, a, I, j, lane);
     flush_count(m, a, nw, lane);
 }
-
 
 // instantiate every group size 1..15 so no predicated-off line is issued
 template <int G>

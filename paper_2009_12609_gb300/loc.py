@@ -82,6 +82,27 @@ class loc_iter_report(ctypes.Structure):
                 ("computed_updates", ctypes.c_double)]
 
 
+class loc_server_opts(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("iters_per_launch", ctypes.c_int), ("window_sigmas", ctypes.c_double),
+                ("device", ctypes.c_int), ("max_queue", ctypes.c_int)]
+
+
+class loc_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("max_rel_dtex", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("n_cells", ctypes.c_int64),
+                ("n_levels", ctypes.c_int), ("updates", ctypes.c_double)]
+
+
+class loc_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("device_bytes_in_use", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("models_per_s", ctypes.c_double)]
+
+
 class LocError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"[{status}] {msg}")
@@ -95,7 +116,8 @@ EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecul
            "loc_iterate", "loc_march", "loc_get_radiation", "loc_get_populations",
            "loc_set_populations", "loc_get_tex", "loc_spectra", "loc_model_info",
            "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
-           "loc_radiation1d_noalloc", "loc_autotune"]
+           "loc_radiation1d_noalloc", "loc_autotune", "loc_server_create",
+           "loc_server_submit", "loc_server_poll", "loc_server_stats", "loc_server_destroy"]
 
 
 def library_path():
@@ -136,6 +158,15 @@ def load():
     lib.loc_radiation1d_noalloc.argtypes = [
         ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
         ctypes.c_double, ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]
+    lib.loc_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(loc_server_opts)]
+    lib.loc_server_submit.argtypes = [_vp, ctypes.POINTER(loc_model_desc),
+                                      ctypes.POINTER(loc_molecule_desc),
+                                      ctypes.POINTER(loc_iter_opts), ctypes.POINTER(ctypes.c_uint64)]
+    lib.loc_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(loc_result),
+                                    _d, ctypes.c_size_t]
+    lib.loc_server_stats.argtypes = [_vp, ctypes.POINTER(loc_server_counters)]
+    lib.loc_server_destroy.argtypes = [_vp]
+    lib.loc_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -449,6 +480,87 @@ class Model:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# --------------------------------------------------------------------------
+# continuous-batching server
+# --------------------------------------------------------------------------
+
+def loc_server_create(max_slots=256, mem_budget_bytes=16 << 30, iters_per_launch=4,
+                      window_sigmas=8.0, device=0, max_queue=0):
+    o = loc_server_opts(int(max_slots), int(mem_budget_bytes), int(iters_per_launch),
+                        float(window_sigmas), int(device), int(max_queue))
+    h = _vp()
+    _check(load().loc_server_create(ctypes.byref(h), ctypes.byref(o)))
+    return h.value
+
+
+def loc_server_submit(h, model, mol, n_levels=None, **opts):
+    keep = _Keep()
+    d = model_desc(model, keep)
+    m = molecule_desc(mol, keep, n_levels)
+    o = iter_opts(**opts)
+    t = ctypes.c_uint64()
+    _check(load().loc_server_submit(h, ctypes.byref(d), ctypes.byref(m), ctypes.byref(o),
+                                    ctypes.byref(t)))
+    return t.value
+
+
+def loc_server_poll(h, ticket, n_cells, n_levels, timeout_ms=60000):
+    r = loc_result()
+    x = np.zeros((int(n_cells), int(n_levels)))
+    _check(load().loc_server_poll(h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r),
+                                  _pd(x), x.size))
+    res = dict(ticket=r.ticket, status=r.status, iterations=r.iterations,
+               max_rel_dtex=r.max_rel_dtex, latency_ms=r.latency_ms, n_cells=r.n_cells,
+               n_levels=r.n_levels, updates=r.updates)
+    return res, x
+
+
+def loc_server_stats(h):
+    c = loc_server_counters()
+    s = load().loc_server_stats(h, ctypes.byref(c))
+    return dict(status=s, submitted=c.submitted, completed=c.completed, active=c.active,
+                queued=c.queued, device_bytes_in_use=c.device_bytes_in_use, p50_ms=c.p50_ms,
+                p99_ms=c.p99_ms, mean_ms=c.mean_ms, models_per_s=c.models_per_s)
+
+
+def loc_server_destroy(h):
+    load().loc_server_destroy(h)
+
+
+class Server:
+    """Owning wrapper of a loc_server; remembers each ticket's result shape."""
+
+    def __init__(self, **opts):
+        self.h = loc_server_create(**opts)
+        self.shape = {}
+
+    def submit(self, model, mol, n_levels=None, **opts):
+        t = loc_server_submit(self.h, model, mol, n_levels, **opts)
+        L = len(mol["g"]) if n_levels is None else int(n_levels)
+        self.shape[t] = (len(model["radius"]), L)
+        return t
+
+    def poll(self, ticket, timeout_ms=60000):
+        K, L = self.shape[ticket]
+        out = loc_server_poll(self.h, ticket, K, L, timeout_ms)
+        self.shape.pop(ticket, None)
+        return out
+
+    def stats(self):
+        return loc_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            loc_server_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self
