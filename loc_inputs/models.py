@@ -185,9 +185,78 @@ def small_grid3d(N=4, n_ch=16, seed=7, box_pc=0.05, abundance=1.0e-4, nside=1):
                         abundance=abundance, nside=nside)
 
 
-def octree_cloud(*args, **kwargs):  # filled in with the octree generator
-    raise NotImplementedError("octree generator not available yet")
+def _octree_from_fields(N, n0, v0, levels, threshold, rng, cascade_ln=0.5, cascade_v_kms=0.2,
+                        refine_mask=None):
+    """Level-ordered octree: level-0 cells in raster order (x fastest), then
+    the 8 children (octant cx + 2 cy + 4 cz) of every refined cell of the
+    previous level, in the order of their parents.  A cell is refined when
+    its density exceeds `threshold` (or where refine_mask says so for the
+    root level) and it is above the deepest level.  Children draw
+    ln n_child = ln n_parent + cascade_ln g - cascade_ln^2 / 2 and
+    v_child = v_parent + cascade_v 2^(-L/3) g_vec (seeded)."""
+    dens = [n0.reshape(-1)]
+    vel = [v0.reshape(-1, 3)]
+    refine = []
+    for L in range(levels + 1):
+        d = dens[L]
+        if L < levels:
+            if L == 0 and refine_mask is not None:
+                r = refine_mask.reshape(-1).astype(np.int32)
+            else:
+                r = (d > threshold).astype(np.int32)
+        else:
+            r = np.zeros(len(d), np.int32)
+        refine.append(r)
+        if L == levels or not r.any():
+            break
+        par = np.flatnonzero(r)
+        ln = np.repeat(np.log(d[par]), 8) + cascade_ln * rng.standard_normal(8 * len(par)) - 0.5 * cascade_ln ** 2
+        dv = cascade_v_kms * KMS * 2.0 ** (-(L + 1) / 3.0)
+        vv = np.repeat(vel[L][par], 8, axis=0) + dv * rng.standard_normal((8 * len(par), 3))
+        dens.append(np.exp(ln))
+        vel.append(vv)
+    n_h2 = np.concatenate(dens)
+    v = np.concatenate(vel)
+    flags = np.concatenate(refine).astype(np.int32)
+    return n_h2, v, flags, len(refine) - 1
 
 
-def small_octree(*args, **kwargs):
-    raise NotImplementedError("octree generator not available yet")
+def octree_cloud(N=64, levels=5, n_ch=64, seed=SEED_BASE + 3, box_pc=1.0, t_kin=15.0,
+                 abundance=1.0e-6, half_width_kms=3.0, nside=2, refine_factor=8.0):
+    """Octree cloud: 64^3 root with the lognormal density and velocity fields of
+    the regular-grid cloud, refined (up to `levels` levels) wherever the
+    density exceeds refine_factor x the mean 1e4 cm^-3; sub-root values from
+    a seeded multiplicative cascade.  Dict keys: geometry "octree3d", n_root,
+    h0, levels, refine[n_cells] (level-ordered flags), per-cell n_h2, t_kin,
+    sigma_turb, abundance, vx, vy, vz, dirs, channel grid, t_bg."""
+    rng = _rng(seed)
+    n0, (vx, vy, vz) = _fields3d(N, seed)
+    v0 = np.stack([vx.reshape(-1), vy.reshape(-1), vz.reshape(-1)], axis=1)
+    n_h2, v, flags, depth = _octree_from_fields(N, n0, v0, levels, refine_factor * 1.0e4, rng)
+    M = len(n_h2)
+    nch, vmin, dv = _channels(n_ch, half_width_kms)
+    return dict(geometry="octree3d", n_root=N, h0=box_pc * PC / N, levels=depth,
+                refine=flags, n_h2=n_h2, t_kin=np.full(M, float(t_kin)),
+                sigma_turb=np.full(M, 0.2 * KMS), abundance=np.full(M, float(abundance)),
+                vx=v[:, 0].copy(), vy=v[:, 1].copy(), vz=v[:, 2].copy(),
+                dirs=healpix_ring_directions(nside), n_ch=nch, v_min=vmin, dv=dv, t_bg=2.73)
+
+
+def small_octree(N=4, levels=2, n_ch=16, seed=11, box_pc=0.05, abundance=1.0e-5, nside=1,
+                 refine_frac=0.3):
+    """A few-cell octree for brute-force and parity tests: about refine_frac
+    of the cells of each level are refined (threshold at that quantile of
+    the level's densities)."""
+    rng = _rng(seed)
+    n0, (vx, vy, vz) = _fields3d(N, seed)
+    v0 = np.stack([vx.reshape(-1), vy.reshape(-1), vz.reshape(-1)], axis=1)
+    thr = float(np.quantile(n0, 1.0 - refine_frac)) if N > 1 else 0.0
+    mask = n0.reshape(-1) > thr if N > 1 else np.ones(1, bool)
+    n_h2, v, flags, depth = _octree_from_fields(N, n0, v0, levels, thr, rng, refine_mask=mask)
+    M = len(n_h2)
+    nch, vmin, dv = _channels(n_ch, 3.0)
+    return dict(geometry="octree3d", n_root=N, h0=box_pc * PC / N, levels=depth,
+                refine=flags, n_h2=n_h2, t_kin=np.full(M, 15.0),
+                sigma_turb=np.full(M, 0.2 * KMS), abundance=np.full(M, float(abundance)),
+                vx=v[:, 0].copy(), vy=v[:, 1].copy(), vz=v[:, 2].copy(),
+                dirs=healpix_ring_directions(nside), n_ch=nch, v_min=vmin, dv=dv, t_bg=2.73)

@@ -311,3 +311,95 @@ def iterate_grid3d(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels
     if bad:
         raise ArithmeticError(f"{bad} singular rate matrices")
     return x, dt[:n_iter]
+
+
+# ---------------------------------------------------------------------------
+# octree
+# ---------------------------------------------------------------------------
+
+def _tree_args(model):
+    refine = np.ascontiguousarray(model["refine"], dtype=np.int32)
+    return int(model["n_root"]), int(model["levels"]), refine
+
+
+def octree_line_segments(model, d, lam, i, j, F=FIXED_BITS):
+    """Segments (z0, dz, cell, level, active) of lattice line (lam, i, j)."""
+    lib = _load()
+    N, Lmax, refine = _tree_args(model)
+    cap = 1 << 16
+    out = np.zeros((cap, 5), np.int64)
+    lib.lo_octree_line_segments.restype = ctypes.c_int64
+    n = lib.lo_octree_line_segments(N, Lmax, int(F), ctypes.c_int64(len(refine)), _p(refine),
+                                    _p(_f64(d)), int(lam), ctypes.c_int64(i), ctypes.c_int64(j),
+                                    _p(out), ctypes.c_int64(cap))
+    if n < 0:
+        raise ValueError("inconsistent refinement flags")
+    return out[:n].copy()
+
+
+def octree_path_sums(model, d, F=FIXED_BITS):
+    """Per-cell total active main-axis path of one direction (int64)."""
+    lib = _load()
+    N, Lmax, refine = _tree_args(model)
+    out = np.zeros(len(refine), np.int64)
+    lib.lo_octree_path_sums.restype = ctypes.c_int64
+    n = lib.lo_octree_path_sums(N, Lmax, int(F), ctypes.c_int64(len(refine)), _p(refine),
+                                _p(_f64(d)), _p(out))
+    if n < 0:
+        raise ValueError("inconsistent refinement flags")
+    return out
+
+
+def leaves(model):
+    return np.flatnonzero(np.asarray(model["refine"]) == 0)
+
+
+def march_octree(mol, model, Kp_leaf, S_leaf, F=FIXED_BITS, n_levels=None):
+    """One ray simulation on an octree; K, S given per leaf [line][leaf];
+    returns SIJ, ESC [line][leaf] and NORM [leaf]."""
+    lib = _load()
+    M = _Mol(mol, n_levels)
+    N, Lmax, refine = _tree_args(model)
+    nc = len(refine)
+    lf = leaves(model)
+    Kp = np.zeros((M.T, nc))
+    S = np.zeros((M.T, nc))
+    Kp[:, lf] = Kp_leaf
+    S[:, lf] = S_leaf
+    SIJ = np.zeros((M.T, nc))
+    ESC = np.zeros((M.T, nc))
+    NORM = np.zeros(nc)
+    dirs = _f64(model["dirs"])
+    r = lib.lo_march_octree(M.ref, N, Lmax, int(F), ctypes.c_int64(nc), _p(refine),
+                            ctypes.c_double(model["h0"]), _p(_f64(model["t_kin"])),
+                            _p(_f64(model["sigma_turb"])), _p(_f64(model["vx"])),
+                            _p(_f64(model["vy"])), _p(_f64(model["vz"])), len(dirs), _p(dirs),
+                            int(model["n_ch"]), ctypes.c_double(model["v_min"]),
+                            ctypes.c_double(model["dv"]), ctypes.c_double(model["t_bg"]),
+                            _p(Kp), _p(S), _p(SIJ), _p(ESC), _p(NORM))
+    if r != 0:
+        raise ValueError("inconsistent refinement flags")
+    return SIJ[:, lf], ESC[:, lf], NORM[lf]
+
+
+def leaf_model(model):
+    """Per-leaf view of an octree model (for line parameters and the SE)."""
+    lf = leaves(model)
+    out = dict(model)
+    for key in ("n_h2", "t_kin", "sigma_turb", "abundance", "vx", "vy", "vz"):
+        out[key] = np.asarray(model[key])[lf]
+    return out
+
+
+def iterate_octree(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels=None):
+    """n_iter ALI iterations on an octree; populations per leaf."""
+    lm = leaf_model(model)
+    x = lte_populations(mol, lm["t_kin"], n_levels) if x0 is None else _f64(x0).copy()
+    dt = np.zeros(n_iter)
+    for it in range(n_iter):
+        Kp, S = line_params(mol, lm, x, n_levels)
+        SIJ, ESC, NORM = march_octree(mol, model, Kp, S, F, n_levels)
+        xn = se_solve(mol, lm, SIJ, ESC, NORM, S, ali, n_levels)
+        dt[it] = max_rel_dtex(mol, x, xn, n_levels)
+        x = xn
+    return x, dt

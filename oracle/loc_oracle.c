@@ -76,7 +76,8 @@ void lo_lte_populations(int n_levels, const double *energy_K, const double *g,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Line profile: "fraction of emitted photons per channel" (Sect. 2).       */
+/* Line profile: the share of the emitted photons falling in each channel   */
+/* (Sect. 2, the practical form of the profile function).                   */
 /* Gaussian of dispersion sigma integrated over channel k, whose velocity   */
 /* interval is [v_min + k dv, v_min + (k+1) dv].  Gas moving with v_los     */
 /* along the ray (towards the observer downstream) is blue-shifted, so the  */
@@ -715,6 +716,369 @@ int lo_iterate_grid3d(const lo_molecule *m, int N, double h0, int F,
     }
     free(Kp); free(S); free(SIJ); free(ESC); free(NORM); free(xn);
     return bad;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* 3D octree grids (Sect. 2.2).                                              */
+/* Cells are level ordered: level-0 cells in raster order (x fastest), then */
+/* the 8 children (octant cx + 2 cy + 4 cz) of every refined level-L cell,   */
+/* in the order of their parents.  A level-L cell is H0 >> L units wide.     */
+/*                                                                           */
+/* Reading of the ray rules (split rays at the upstream border of a refined  */
+/* cell, side rays, recursive splitting, termination on coarsening, periodic */
+/* re-entry): lattice lines exist at every level L, at                       */
+/* A(z) = o + i (H0 >> L) + floor(q_a z / 2^F) with the common offset        */
+/* o = (H0 >> Lmax) / 2, so the level-L lattice contains the level-(L-1) one.*/
+/* A line's creation level lambda is the coarsest level whose lattice holds  */
+/* it.  A line is active in a leaf iff the leaf's level >= lambda: then every*/
+/* level-L leaf is crossed by exactly the level-L lattice, which is what the */
+/* split, side and termination rules achieve, and the path length per cell  */
+/* and direction is exactly H_L.  A line that becomes active on entering a  */
+/* leaf c (after being inactive, or at the model's upstream face) starts     */
+/* with the intensity of its parent: the level-(lambda-1) lattice line that  */
+/* crosses the upstream face of C, the level-(lambda-1) ancestor of c, taken */
+/* where it crosses that face (for lambda = 0: the background).  Photon     */
+/* splitting into 1/4 and scaling by 4^-dL on termination leave the          */
+/* intensity unchanged.                                                      */
+/*                                                                           */
+/* The oracle walks every lattice line of every level through the whole    */
+/* model (pass 1: segments, activation events and parents), then follows    */
+/* the lines in order of creation level (pass 2), so a parent's intensity at */
+/* each requested face is known before its children start.                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int N, Lmax, F;
+    int64_t n_cells;
+    int64_t *child;       /* first child or -1 */
+} lo_tree;
+
+static int lo_tree_build(lo_tree *t, int N, int Lmax, int F, int64_t n_cells, const int32_t *refine)
+{
+    t->N = N; t->Lmax = Lmax; t->F = F; t->n_cells = n_cells;
+    t->child = (int64_t *)malloc(sizeof(int64_t) * n_cells);
+    int64_t nxt = (int64_t)N * N * N;
+    for (int64_t c = 0; c < n_cells; c++) {
+        if (refine[c]) { t->child[c] = nxt; nxt += 8; }
+        else t->child[c] = -1;
+    }
+    return (nxt == n_cells) ? 0 : -1;
+}
+
+/* leaf containing the original-coordinate point; *level receives its level */
+static int64_t lo_tree_locate(const lo_tree *t, int64_t x, int64_t y, int64_t z, int max_level, int *level)
+{
+    const int F = t->F, N = t->N;
+    int64_t c = ((z >> F) * N + (y >> F)) * N + (x >> F);
+    int L = 0;
+    while (t->child[c] >= 0 && L < max_level) {
+        L++;
+        const int sh = F - L;
+        const int oct = (int)(((x >> sh) & 1) | (((y >> sh) & 1) << 1) | (((z >> sh) & 1) << 2));
+        c = t->child[c] + oct;
+    }
+    *level = L;
+    return c;
+}
+
+typedef struct { int64_t z0, dz, cell; int level, active; } lo_oseg;
+typedef struct { int lam; int64_t i, j, seg0, nseg; } lo_oline;
+typedef struct { int64_t line, seg, parent, z_face, snap; } lo_oevent;
+
+typedef struct {
+    lo_oline *lines; int64_t n_lines;
+    lo_oseg *segs; int64_t n_segs, cap_segs;
+    lo_oevent *ev; int64_t n_ev, cap_ev;
+    int64_t **table;      /* [lambda][i * M + j] -> line id (-1 for coarser lines) */
+} lo_odir;
+
+/* mirrored coordinates (ray moving +m, +a, +b) -> original, per axis */
+static int64_t lo_unmirror(const lo_dirinfo *di, int ax, int64_t v, int64_t E)
+{
+    return di->flip[ax] ? E - 1 - v : v;
+}
+
+/* original-axis cell lower corner -> mirrored lower corner */
+static int64_t lo_mirror_lo(const lo_dirinfo *di, int ax, int64_t lo, int64_t H, int64_t E)
+{
+    return di->flip[ax] ? E - lo - H : lo;
+}
+
+static void lo_point(const lo_dirinfo *di, int64_t z, int64_t Au, int64_t Bu, int64_t E, int64_t p[3])
+{
+    int64_t m[3];
+    m[di->m] = z; m[di->a] = Au % E; m[di->b] = Bu % E;
+    for (int ax = 0; ax < 3; ax++) p[ax] = lo_unmirror(di, ax, m[ax], E);
+}
+
+static int64_t lo_floorq(int64_t q, int64_t z, int F) { return (int64_t)(((__int128)q * z) >> F); }
+
+static void lo_push_seg(lo_odir *D, lo_oseg sg)
+{
+    if (D->n_segs == D->cap_segs) {
+        D->cap_segs = D->cap_segs ? 2 * D->cap_segs : 4096;
+        D->segs = (lo_oseg *)realloc(D->segs, sizeof(lo_oseg) * D->cap_segs);
+    }
+    D->segs[D->n_segs++] = sg;
+}
+
+static void lo_push_ev(lo_odir *D, lo_oevent e)
+{
+    if (D->n_ev == D->cap_ev) {
+        D->cap_ev = D->cap_ev ? 2 * D->cap_ev : 1024;
+        D->ev = (lo_oevent *)realloc(D->ev, sizeof(lo_oevent) * D->cap_ev);
+    }
+    D->ev[D->n_ev++] = e;
+}
+
+/* walk line (lam, i, j) from z = 0 to E through the leaves, appending segments */
+static void lo_walk_octree_line(const lo_tree *t, const lo_dirinfo *di, int lam, int64_t i, int64_t j, lo_odir *D)
+{
+    const int F = t->F;
+    const int64_t H0 = (int64_t)1 << F;
+    const int64_t E = (int64_t)t->N * H0;
+    const int64_t o = (H0 >> t->Lmax) / 2;
+    const int64_t A0 = o + i * (H0 >> lam), B0 = o + j * (H0 >> lam);
+    int64_t z = 0;
+    while (z < E) {
+        const int64_t Au = A0 + lo_floorq(di->qa, z, F);
+        const int64_t Bu = B0 + lo_floorq(di->qb, z, F);
+        int64_t p[3];
+        lo_point(di, z, Au, Bu, E, p);
+        int L;
+        const int64_t c = lo_tree_locate(t, p[0], p[1], p[2], t->Lmax, &L);
+        const int64_t HL = H0 >> L;
+        int64_t mlo[3];
+        for (int ax = 0; ax < 3; ax++) mlo[ax] = lo_mirror_lo(di, ax, (p[ax] / HL) * HL, HL, E);
+        int64_t zn = mlo[di->m] + HL;
+        {
+            const int64_t am = Au % E;
+            const int64_t target = Au - am + mlo[di->a] + HL - A0;
+            const int64_t za = lo_next_cross(di->qa, F, target);
+            if (za < zn) zn = za;
+        }
+        {
+            const int64_t bm = Bu % E;
+            const int64_t target = Bu - bm + mlo[di->b] + HL - B0;
+            const int64_t zb = lo_next_cross(di->qb, F, target);
+            if (zb < zn) zn = zb;
+        }
+        if (zn > E) zn = E;
+        lo_oseg sg = {z, zn - z, c, L, L >= lam};
+        lo_push_seg(D, sg);
+        z = zn;
+    }
+}
+
+static int lo_creation_level(int lam, int64_t i, int64_t j)
+{
+    while (lam > 0 && (i % 2) == 0 && (j % 2) == 0) { lam--; i /= 2; j /= 2; }
+    return lam;
+}
+
+/* pass 1 for one direction */
+static void lo_octree_geometry(const lo_tree *t, const double *d, lo_odir *D)
+{
+    memset(D, 0, sizeof(*D));
+    lo_dirinfo di;
+    lo_direction_info(d, t->F, &di);
+    const int F = t->F, Lmax = t->Lmax;
+    const int64_t H0 = (int64_t)1 << F;
+    const int64_t E = (int64_t)t->N * H0;
+    const int64_t o = (H0 >> Lmax) / 2;
+    /* line ids in order of creation level */
+    D->table = (int64_t **)malloc(sizeof(int64_t *) * (Lmax + 1));
+    int64_t nl = 0;
+    for (int lam = 0; lam <= Lmax; lam++) {
+        const int64_t M = (int64_t)t->N << lam;
+        D->table[lam] = (int64_t *)malloc(sizeof(int64_t) * M * M);
+        for (int64_t i = 0; i < M; i++)
+            for (int64_t j = 0; j < M; j++)
+                D->table[lam][i * M + j] = (lo_creation_level(lam, i, j) == lam) ? nl++ : -1;
+    }
+    D->n_lines = nl;
+    D->lines = (lo_oline *)malloc(sizeof(lo_oline) * nl);
+    for (int lam = 0; lam <= Lmax; lam++) {
+        const int64_t M = (int64_t)t->N << lam;
+        for (int64_t i = 0; i < M; i++)
+            for (int64_t j = 0; j < M; j++) {
+                const int64_t id = D->table[lam][i * M + j];
+                if (id < 0) continue;
+                lo_oline *ln = &D->lines[id];
+                ln->lam = lam; ln->i = i; ln->j = j;
+                ln->seg0 = D->n_segs;
+                lo_walk_octree_line(t, &di, lam, i, j, D);
+                ln->nseg = D->n_segs - ln->seg0;
+            }
+    }
+    /* activation events */
+    for (int64_t id = 0; id < nl; id++) {
+        const lo_oline *ln = &D->lines[id];
+        for (int64_t k = 0; k < ln->nseg; k++) {
+            const lo_oseg *sg = &D->segs[ln->seg0 + k];
+            if (!sg->active) continue;
+            if (k > 0 && D->segs[ln->seg0 + k - 1].active) continue;
+            lo_oevent e = {id, ln->seg0 + k, -1, 0, D->n_ev};
+            if (ln->lam > 0) {
+                const int lp = ln->lam - 1;
+                const int64_t Hp = H0 >> lp;
+                const int64_t Au = o + ln->i * (H0 >> ln->lam) + lo_floorq(di.qa, sg->z0, F);
+                const int64_t Bu = o + ln->j * (H0 >> ln->lam) + lo_floorq(di.qb, sg->z0, F);
+                int64_t p[3];
+                lo_point(&di, sg->z0, Au, Bu, E, p);
+                int Lc;
+                const int64_t C = lo_tree_locate(t, p[0], p[1], p[2], lp, &Lc);
+                (void)C;
+                int64_t mlo[3];
+                for (int ax = 0; ax < 3; ax++) mlo[ax] = lo_mirror_lo(&di, ax, (p[ax] / Hp) * Hp, Hp, E);
+                const int64_t zf = mlo[di.m];
+                const int64_t Mp = (int64_t)t->N << lp;
+                int64_t Da = (mlo[di.a] - o - lo_floorq(di.qa, zf, F)) % E; if (Da < 0) Da += E;
+                int64_t Db = (mlo[di.b] - o - lo_floorq(di.qb, zf, F)) % E; if (Db < 0) Db += E;
+                int64_t ip = ((Da + Hp - 1) / Hp) % Mp, jp = ((Db + Hp - 1) / Hp) % Mp;
+                int lpp = lp;
+                while (lpp > 0 && (ip % 2) == 0 && (jp % 2) == 0) { lpp--; ip /= 2; jp /= 2; }
+                e.parent = D->table[lpp][ip * ((int64_t)t->N << lpp) + jp];
+                e.z_face = zf;
+            }
+            lo_push_ev(D, e);
+        }
+    }
+}
+
+static void lo_odir_free(lo_odir *D, int Lmax)
+{
+    for (int lam = 0; lam <= Lmax; lam++) free(D->table[lam]);
+    free(D->table); free(D->lines); free(D->segs); free(D->ev);
+}
+
+/* Exported for tests: number of lines and segments of a direction, and the
+ * segments (z0, dz, cell, level, active) of line (lam, i, j). */
+int64_t lo_octree_line_segments(int N, int Lmax, int F, int64_t n_cells, const int32_t *refine,
+                                const double *d, int lam, int64_t i, int64_t j, int64_t *out5, int64_t cap)
+{
+    lo_tree t;
+    if (lo_tree_build(&t, N, Lmax, F, n_cells, refine) != 0) { free(t.child); return -1; }
+    lo_dirinfo di;
+    lo_direction_info(d, F, &di);
+    lo_odir D;
+    memset(&D, 0, sizeof(D));
+    lo_walk_octree_line(&t, &di, lam, i, j, &D);
+    const int64_t n = D.n_segs;
+    for (int64_t k = 0; k < n && k < cap; k++) {
+        out5[5 * k + 0] = D.segs[k].z0; out5[5 * k + 1] = D.segs[k].dz; out5[5 * k + 2] = D.segs[k].cell;
+        out5[5 * k + 3] = D.segs[k].level; out5[5 * k + 4] = D.segs[k].active;
+    }
+    free(D.segs); free(t.child);
+    return n;
+}
+
+/* Exported for tests: per-cell sum of active main-axis path over all lines of
+ * one direction (int64 [n_cells]); returns the number of active segments. */
+int64_t lo_octree_path_sums(int N, int Lmax, int F, int64_t n_cells, const int32_t *refine,
+                            const double *d, int64_t *sum_dz)
+{
+    lo_tree t;
+    if (lo_tree_build(&t, N, Lmax, F, n_cells, refine) != 0) { free(t.child); return -1; }
+    lo_odir D;
+    lo_octree_geometry(&t, d, &D);
+    memset(sum_dz, 0, sizeof(int64_t) * n_cells);
+    int64_t na = 0;
+    for (int64_t k = 0; k < D.n_segs; k++)
+        if (D.segs[k].active) { sum_dz[D.segs[k].cell] += D.segs[k].dz; na++; }
+    lo_odir_free(&D, Lmax);
+    free(t.child);
+    return na;
+}
+
+/* One radiation-field simulation on an octree (Sect. 2.2).  Per-cell arrays
+ * are level ordered over all cells (values of refined cells unused);
+ * outputs SIJ, ESC [line][cell] and NORM [cell] (zero on refined cells).
+ * Returns 0, or -1 for an inconsistent refinement array. */
+int lo_march_octree(const lo_molecule *m, int N, int Lmax, int F, int64_t n_cells, const int32_t *refine,
+                    double h0, const double *t_kin, const double *sigma_turb,
+                    const double *vx, const double *vy, const double *vz,
+                    int n_dir, const double *dirs, int n_ch, double v_min, double dv, double t_bg,
+                    const double *Kp, const double *S, double *SIJ, double *ESC, double *NORM)
+{
+    const int T = m->n_lines;
+    lo_tree t;
+    if (lo_tree_build(&t, N, Lmax, F, n_cells, refine) != 0) { free(t.child); return -1; }
+    const int64_t H0 = (int64_t)1 << F;
+    memset(SIJ, 0, sizeof(double) * T * n_cells);
+    memset(ESC, 0, sizeof(double) * T * n_cells);
+    memset(NORM, 0, sizeof(double) * n_cells);
+    for (int id = 0; id < n_dir; id++) {
+        const double *d = dirs + 3 * id;
+        lo_dirinfo di;
+        lo_direction_info(d, F, &di);
+        const double unit = h0 / (double)H0 / fabs(d[di.m]);
+        lo_odir D;
+        lo_octree_geometry(&t, d, &D);
+        /* snapshot requests per parent line, and each event's snapshot slot */
+        int64_t *req_n = (int64_t *)calloc(D.n_lines + 1, sizeof(int64_t));
+        for (int64_t e = 0; e < D.n_ev; e++) if (D.ev[e].parent >= 0) req_n[D.ev[e].parent + 1]++;
+        for (int64_t l = 0; l < D.n_lines; l++) req_n[l + 1] += req_n[l];
+        int64_t *req_ev = (int64_t *)malloc(sizeof(int64_t) * (D.n_ev + 1));
+        int64_t *fill = (int64_t *)calloc(D.n_lines, sizeof(int64_t));
+        for (int64_t e = 0; e < D.n_ev; e++) {
+            const int64_t p = D.ev[e].parent;
+            if (p >= 0) req_ev[req_n[p] + fill[p]++] = e;
+        }
+        /* event index of each segment that starts an active interval */
+        int64_t *seg_ev = (int64_t *)malloc(sizeof(int64_t) * (D.n_segs + 1));
+        for (int64_t k = 0; k < D.n_segs; k++) seg_ev[k] = -1;
+        for (int64_t e = 0; e < D.n_ev; e++) seg_ev[D.ev[e].seg] = e;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int tt = 0; tt < T; tt++) {
+            const double nbg = lo_bg_occupation(m->line_nu[tt], t_bg);
+            double *snap = (double *)malloc(sizeof(double) * (D.n_ev + 1) * n_ch);
+            double *I = (double *)malloc(sizeof(double) * n_ch);
+            double *phi = (double *)malloc(sizeof(double) * n_ch);
+            for (int64_t l = 0; l < D.n_lines; l++) {      /* lines are in creation-level order */
+                const lo_oline *ln = &D.lines[l];
+                for (int k = 0; k < n_ch; k++) I[k] = nbg;
+                for (int64_t q = 0; q < ln->nseg; q++) {
+                    const int64_t sk = ln->seg0 + q;
+                    const lo_oseg *sg = &D.segs[sk];
+                    const int64_t e = seg_ev[sk];
+                    if (e >= 0) {                           /* activation */
+                        if (D.ev[e].parent < 0) for (int k = 0; k < n_ch; k++) I[k] = nbg;
+                        else for (int k = 0; k < n_ch; k++) I[k] = snap[D.ev[e].snap * n_ch + k];
+                    }
+                    if (!sg->active) continue;
+                    /* children waiting for this line's intensity at this face */
+                    for (int64_t r = req_n[l]; r < req_n[l + 1]; r++) {
+                        const int64_t ce = req_ev[r];
+                        if (D.ev[ce].z_face == sg->z0)
+                            for (int k = 0; k < n_ch; k++) snap[ce * n_ch + k] = I[k];
+                    }
+                    const int64_t c = sg->cell;
+                    const double sig = lo_sigma(sigma_turb[c], t_kin[c], m->mass_amu);
+                    const double vlos = vx[c] * d[0] + vy[c] * d[1] + vz[c] * d[2];
+                    lo_profile(n_ch, v_min, dv, vlos, sig, phi);
+                    const double s = (double)sg->dz * unit;
+                    const double w = (double)sg->dz / ((double)(H0 >> sg->level) * n_dir);
+                    double sij1 = 0.0, esc1 = 0.0;
+                    lo_step(1, n_ch, 1, 0, phi, s, w, Kp + (size_t)tt * n_cells + c, S + (size_t)tt * n_cells + c,
+                            I, &sij1, &esc1, NULL);
+                    SIJ[(size_t)tt * n_cells + c] += sij1;
+                    ESC[(size_t)tt * n_cells + c] += esc1;
+                    if (tt == 0) {
+                        double sp = 0.0;
+                        for (int k = 0; k < n_ch; k++) sp += phi[k];
+                        NORM[c] += w * sp;
+                    }
+                }
+            }
+            free(snap); free(I); free(phi);
+        }
+        /* every event must have received its snapshot (parent active at the face) */
+        free(req_n); free(req_ev); free(fill); free(seg_ev);
+        lo_odir_free(&D, Lmax);
+    }
+    free(t.child);
+    return 0;
 }
 
 int lo_num_threads(void)
