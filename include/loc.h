@@ -62,7 +62,9 @@ typedef struct loc_allocator {
 
 /*
  * Model description (Sect. 2.1 for shells, Sect. 2.2 for 3D grids).
- *  geometry     LOC_SHELLS_1D or LOC_GRID_3D (LOC_OCTREE_3D: see octree_*).
+ *  geometry     LOC_SHELLS_1D, LOC_GRID_3D or LOC_OCTREE_3D (see octree_*);
+ *               for octrees the model's cells (populations, radiation,
+ *               T_ex) are the leaves, in level-ordered cell order.
  *  n_shells     1D: number of concentric shells K >= 1.
  *  radius       1D: [K] outer radii, strictly increasing, > 0.
  *  n_rays       1D: number of equidistant impact parameters
@@ -71,7 +73,8 @@ typedef struct loc_allocator {
  *               are indexed x fastest: idx = (iz N + iy) N + ix.
  *  n_dir, dirs  3D: [n_dir][3] unit ray directions (e.g. HEALPix centres).
  *  octree_levels, octree_refine, octree_n_cells
- *               octree: number of levels below the root, and per cell a
+ *               octree (1 <= n_root <= 255, levels <= 10): number of
+ *               levels below the root, and per cell a
  *               refine flag (0 = leaf, 1 = split into 8 children) in level
  *               order: level-0 cells in raster order, then the children of
  *               every refined level-L cell, in the order of their parents,
@@ -350,6 +353,22 @@ loc_status loc_server_stats(loc_server *s, loc_server_counters *st);
 
 /* Stop the server: running and queued requests are abandoned. */
 void loc_server_destroy(loc_server *s);
+
+/* Active segments of one direction of an octree model (Sect. 2.2), traced
+ * on the device by the same traversal the march uses (root rays, rays
+ * created at refined cells, terminations).  Record k of out7 is
+ * {creation level, i, j, z0, dz, leaf, leaf level}: the lattice line
+ * (level, i, j), its segment start z0 and length dz in fixed-point units
+ * (one root cell = 2^24), and the leaf index (leaves numbered in the
+ * level-ordered cell order).  *n_seg receives the total count; at most cap
+ * records are written (beyond cap an unspecified subset is kept, which
+ * serves for sampling). */
+loc_status loc_trace_octree(const loc_model *m, int dir, int64_t *out7, int64_t cap, int64_t *n_seg);
+
+/* Per-leaf total main-axis length (fixed-point units) of the active
+ * segments of one direction of an octree model: the constant-path-length
+ * property (Sect. 2.2) makes it exactly 2^24 >> level for every leaf. */
+loc_status loc_octree_path_sums(const loc_model *m, int dir, int64_t *out, size_t n_out);
 
 /* Wait for all queued work of the model. */
 loc_status loc_sync(loc_model *m);

@@ -217,6 +217,8 @@ __global__ void dir_setup_kernel(const double *dirs, int n_dir, double h0, Dir3D
     D.Db = (long long)(step / qb); D.rb = (long long)(step % qb);
     D.Qa0 = (long long)(first / qa); D.Ra0 = (long long)(first % qa);
     D.Qb0 = (long long)(first / qb); D.Rb0 = (long long)(first % qb);
+    D.ma = ~0ull / qa;
+    D.mb = ~0ull / qb;
     D.unit = (float)(h0 / scale / fabs(d[mm]));
     out[id] = D;
 }

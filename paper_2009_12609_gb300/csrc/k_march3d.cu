@@ -93,6 +93,7 @@ loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st)
         return LOC_EINVAL;
     }
     if (m.geometry == LOC_SHELLS_1D) return launch_march1d(m, a, st);
+    if (m.geometry == LOC_OCTREE_3D) return launch_march_octree(m, a, st);
     return launch_march3d(m, a, st);
 }
 

@@ -1,0 +1,458 @@
+// k_octree.cu -- ray march over octree grids (Sect. 2.2).
+//
+// Ray lattice as for regular grids (walk3d.cuh), at every refinement level:
+// line (lam, i, j) passes through A(z) = o + i (H0 >> lam) + floor(q_a z / 2^F)
+// (likewise B) with the common offset o = (H0 >> Lmax) / 2, so coarser
+// lattices are contained in finer ones.  A line's creation level lam is the
+// coarsest level whose lattice holds it; it is active in a leaf iff the leaf's
+// level >= lam.  This is the effect of the paper's rules -- rays split into
+// four at the upstream border of a refined cell, side rays added where a
+// neighbour is less refined, rays terminated on entering coarser cells,
+// re-entry on the opposite side -- and gives every level-L leaf exactly the
+// level-L lattice, i.e. a constant path length per cell and direction.
+//
+// Every refined cell C (level k) is entered through its upstream face by
+// exactly one active line of level <= k.  When that line reaches the face it
+// creates C's new rays: the level-(k+1) lines that become active inside C,
+// through the face (split) or through a side face (side rays), each
+// starting with the creating line's intensity at the face.  New rays are
+// followed first (depth first, "higher levels first"), then the creating
+// line resumes: one stack frame per refinement level, holding one intensity
+// snapshot that both initialises the new rays and restores the parent.
+//
+// GB300 mapping: persistent warps take (direction, root line, line group)
+// items from a counter; lanes over channels in the per-step update
+// (march_step, shared with the other geometries); the 25 candidate lines of
+// a refined cell are examined one per lane (entry point, and whether the line
+// was inactive just before -- one octree descent each) and collected with a
+// ballot; point location is an integer descent through the child array.
+#include "k_march.cuh"
+
+namespace loc {
+
+constexpr int kOctWarpsPerBlock = 4;
+constexpr int kOctBlocksPerSM = 4;
+constexpr int kOctMaxDepth = 10;
+
+// floor(n / q) with minv = floor((2^64 - 1) / q): one correction step
+__device__ __forceinline__ unsigned long long udivq(unsigned long long n, unsigned long long q,
+                                                    unsigned long long minv)
+{
+    unsigned long long t = __umul64hi(n, minv);
+    if (n - t * q >= q) t++;
+    return t;
+}
+
+// smallest z with floor(q z / 2^F) >= target (target >= 1, q > 0)
+__device__ __forceinline__ long long cross_z(long long target, long long q, unsigned long long minv)
+{
+    const unsigned long long num = ((unsigned long long)target << kFixedBits) + (unsigned long long)q - 1ull;
+    return (long long)udivq(num, (unsigned long long)q, minv);
+}
+
+__device__ __forceinline__ long long fq(long long q, long long z) { return (q * z) >> kFixedBits; }
+
+struct OctGeo {
+    Dir3D D;
+    long long E, o;
+    int N, Lmax;
+};
+
+__device__ __forceinline__ void oct_point(const OctGeo &g, long long Au, long long Bu, long long z, long long p[3])
+{
+    long long mm[3];
+    mm[g.D.m] = z;
+    mm[g.D.a] = Au % g.E;
+    mm[g.D.b] = Bu % g.E;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) p[ax] = g.D.flip[ax] ? g.E - 1 - mm[ax] : mm[ax];
+}
+
+// cell containing p, descending at most max_level levels; level receives it
+__device__ __forceinline__ int oct_locate(const DevModel &m, const OctGeo &g, const long long p[3],
+                                          int max_level, int &level)
+{
+    const int F = kFixedBits;
+    int c = (int)(((p[2] >> F) * g.N + (p[1] >> F)) * g.N + (p[0] >> F));
+    int L = 0;
+    while (L < max_level) {
+        const int ch = __ldg(m.child + c);
+        if (ch < 0) break;
+        L++;
+        const int sh = F - L;
+        c = ch + (int)(((p[0] >> sh) & 1) | (((p[1] >> sh) & 1) << 1) | (((p[2] >> sh) & 1) << 2));
+    }
+    level = L;
+    return c;
+}
+
+// mirrored lower corner of the level-L box containing original coordinate v
+__device__ __forceinline__ long long oct_mlo(const OctGeo &g, int ax, long long v, int L)
+{
+    const int sh = kFixedBits - L;
+    const long long H = 1ll << sh;
+    const long long lo = (v >> sh) << sh;
+    return g.D.flip[ax] ? g.E - lo - H : lo;
+}
+
+struct OctLine {
+    int lam, i, j;
+    long long z;
+};
+
+// Per-warp frame of the depth-first traversal (shared memory).
+struct OctFrame {
+    int lam, i, j;          // paused creating line
+    long long z;            // its position (the face where it created rays)
+    int n_kids, next;       // new rays of this frame, next one to start
+};
+
+// Creates the rays of refined cell (level k) entered by line `cur` at its
+// upstream face cur.z; appends them to kids[] from index *nk.  All lanes.
+__device__ __forceinline__ void oct_spawn(const DevModel &m, const OctGeo &g, const OctLine &cur,
+                                          const long long p[3], int k, int4 *kids, int &nk, int lane)
+{
+    const long long H0 = 1ll << kFixedBits;
+    const long long H = H0 >> k, Hc = H >> 1;
+    const long long zf = cur.z;
+    const long long ma0 = oct_mlo(g, g.D.a, p[g.D.a], k);
+    const long long mb0 = oct_mlo(g, g.D.b, p[g.D.b], k);
+    const long long fa = fq(g.D.qa, zf), fb = fq(g.D.qb, zf);
+    const long long da = fq(g.D.qa, zf + H - 1) - fa, db = fq(g.D.qb, zf + H - 1) - fb;
+    const long long Mc = (long long)g.N << (k + 1);
+    // first candidate index along each axis: lattice position >= box lower bound - drift
+    long long xa = (ma0 - da - g.o - fa) % g.E;
+    if (xa < 0) xa += g.E;
+    long long xb = (mb0 - db - g.o - fb) % g.E;
+    if (xb < 0) xb += g.E;
+    const long long ia0 = (xa + Hc - 1) / Hc, jb0 = (xb + Hc - 1) / Hc;
+    bool is_new = false;
+    int ci = 0, cj = 0;
+    long long zin = 0;
+    // at most 4 lattice lines per axis can meet the box; small lattices (fewer
+    // than 5 lines) are enumerated once each instead of wrapping onto themselves
+    const int nu = (int)min(5ll, Mc);
+    const int cu = lane / 5, cv = lane % 5;
+    if (lane < 25 && cu < nu && cv < nu) {
+        ci = (int)((ia0 + cu) % Mc);
+        cj = (int)((jb0 + cv) % Mc);
+        if ((ci & 1) || (cj & 1)) {                      // creation level k + 1
+            const long long A0 = g.o + (long long)ci * Hc, B0 = g.o + (long long)cj * Hc;
+            // offset from the box's lower bound: [0, H) inside, otherwise taken
+            // as before the box (the line may still drift into it)
+            long long ar = (A0 + fa - ma0) % g.E;
+            if (ar < 0) ar += g.E;
+            if (ar >= H) ar -= g.E;
+            long long br = (B0 + fb - mb0) % g.E;
+            if (br < 0) br += g.E;
+            if (br >= H) br -= g.E;
+            const long long NEVER = 1ll << 62;
+            bool ok = (ar >= -da) && (ar < H) && (br >= -db) && (br < H);
+            long long za_in = zf, zb_in = zf, za_out = NEVER, zb_out = NEVER;
+            if (ok) {
+                if (ar < 0) za_in = (g.D.qa > 0) ? cross_z(fa - ar, g.D.qa, g.D.ma) : NEVER;
+                if (br < 0) zb_in = (g.D.qb > 0) ? cross_z(fb - br, g.D.qb, g.D.mb) : NEVER;
+                if (g.D.qa > 0) za_out = cross_z(fa - ar + H, g.D.qa, g.D.ma);
+                if (g.D.qb > 0) zb_out = cross_z(fb - br + H, g.D.qb, g.D.mb);
+                zin = max(zf, max(za_in, zb_in));
+                const long long zout = min(zf + H, min(za_out, zb_out));
+                ok = zin < zout;
+            }
+            if (ok) {
+                if (zin == 0) {
+                    is_new = true;
+                } else {                                  // inactive just before entering?
+                    long long q[3];
+                    oct_point(g, A0 + fq(g.D.qa, zin - 1), B0 + fq(g.D.qb, zin - 1), zin - 1, q);
+                    int lev;
+                    oct_locate(m, g, q, k + 1, lev);
+                    is_new = lev < k + 1;
+                }
+            }
+        }
+    }
+    const unsigned mask = __ballot_sync(kFull, is_new);
+    if (is_new) {
+        const int slot = nk + __popc(mask & ((1u << lane) - 1u));
+        if (slot < kOctMaxKids) kids[slot] = make_int4(k + 1, ci, cj, (int)(unsigned)zin);
+    }
+    nk += __popc(mask);
+}
+
+struct OctMarchVisitor {
+    static constexpr bool kNeedI = true;
+};
+
+struct OctTraceVisitor {
+    static constexpr bool kNeedI = false;
+    long long *out;            // records {level, i, j, z0, dz, leaf, leaf level}
+    long long cap;
+    unsigned long long *count;
+    unsigned long long *sums;  // optional per-leaf sum of dz
+    int dir;
+};
+
+// Depth-first traversal of the rays created from root line (i, j).
+template <int G, class V>
+__device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo &g, int i, int j,
+                             float *I, float *snap, int4 *kids_all, OctFrame *fr, int lane, V &vis,
+                             long long &nw)
+{
+    const long long H0 = 1ll << kFixedBits;
+    const int snap_n = a.per * m.n_ch;
+    const float wscale = 1.0f / (float)m.n_dir;
+    OctLine cur = {0, i, j, 0};
+    long long skip_z = -1;          // a resumed line does not create rays twice at one face
+    int depth = 0;
+    if (V::kNeedI) init_ray<G>(m, a, I, lane);
+    while (true) {
+        bool done_line = cur.z >= g.E;
+        long long p[3];
+        int Lc = 0;
+        int cell = 0;
+        long long Au = 0, Bu = 0;
+        if (!done_line) {
+            Au = g.o + (long long)cur.i * (H0 >> cur.lam) + fq(g.D.qa, cur.z);
+            Bu = g.o + (long long)cur.j * (H0 >> cur.lam) + fq(g.D.qb, cur.z);
+            oct_point(g, Au, Bu, cur.z, p);
+            cell = oct_locate(m, g, p, g.Lmax, Lc);
+            done_line = Lc < cur.lam;                       // entered a coarser leaf: terminated
+        }
+        if (!done_line && cur.z != skip_z) {
+            // new rays of the refined cells whose upstream face this line enters now
+            // (a line at depth d has creation level >= d, so depth < Lmax here)
+            int nk = 0;
+            if (depth < kOctMaxDepth) {
+                int4 *kids = kids_all + depth * kOctMaxKids;
+                for (int k = cur.lam; k < Lc; k++)
+                    if (oct_mlo(g, g.D.m, p[g.D.m], k) == cur.z) oct_spawn(m, g, cur, p, k, kids, nk, lane);
+            } else {
+                for (int k = cur.lam; k < Lc; k++)
+                    if (oct_mlo(g, g.D.m, p[g.D.m], k) == cur.z && lane == 0) atomicExch(m.oct_err, 3);
+            }
+            if (nk > kOctMaxKids) {
+                if (lane == 0) atomicExch(m.oct_err, 1);
+                nk = kOctMaxKids;
+            }
+            if (nk > 0) {
+                if (depth >= kOctMaxDepth) {
+                    if (lane == 0) atomicExch(m.oct_err, 2);
+                } else {
+                    if (lane == 0) {
+                        fr[depth].lam = cur.lam; fr[depth].i = cur.i; fr[depth].j = cur.j;
+                        fr[depth].z = cur.z; fr[depth].n_kids = nk; fr[depth].next = 0;
+                    }
+                    if (V::kNeedI) {
+                        float *sn = snap + (size_t)depth * snap_n;
+                        for (int q = lane; q < snap_n; q += 32) sn[q] = I[q];
+                    }
+                    depth++;
+                    __syncwarp();
+                    done_line = true;                       // switch to the first new ray below
+                    skip_z = -1;
+                }
+            }
+        }
+        if (!done_line) {
+            // one step through leaf `cell`
+            const long long HL = H0 >> Lc;
+            long long zn = oct_mlo(g, g.D.m, p[g.D.m], Lc) + HL;
+            if (g.D.qa > 0) {
+                const long long T = Au - (Au % g.E) + oct_mlo(g, g.D.a, p[g.D.a], Lc) + HL;
+                zn = min(zn, cross_z(T - (Au - fq(g.D.qa, cur.z)), g.D.qa, g.D.ma));
+            }
+            if (g.D.qb > 0) {
+                const long long T = Bu - (Bu % g.E) + oct_mlo(g, g.D.b, p[g.D.b], Lc) + HL;
+                zn = min(zn, cross_z(T - (Bu - fq(g.D.qb, cur.z)), g.D.qb, g.D.mb));
+            }
+            zn = min(zn, g.E);
+            const long long dz = zn - cur.z;
+            const int leaf = __ldg(m.leaf_of + cell);
+            if constexpr (V::kNeedI) {
+                Step<G> st;
+                st.cell = leaf;
+                const float4 cv = m.vel[leaf];
+                st.vlos = cv.x * g.D.d[0] + cv.y * g.D.d[1] + cv.z * g.D.d[2];
+                st.inv = cv.w;
+                st.s = (float)dz * g.D.unit;
+                st.w = (float)dz / (float)HL * wscale;
+                load_lines<G>(m, a, st);
+                nw += march_step<G>(m, a, I, st, lane);
+                __syncwarp();
+            } else {
+                if (lane == 0) {
+                    if (vis.sums) atomicAdd(vis.sums + leaf, (unsigned long long)dz);
+                    const unsigned long long n = atomicAdd(vis.count, 1ull);
+                    if ((long long)n < vis.cap) {
+                        long long *o = vis.out + 7 * n;
+                        o[0] = cur.lam; o[1] = cur.i; o[2] = cur.j; o[3] = cur.z; o[4] = dz;
+                        o[5] = leaf; o[6] = Lc;
+                    }
+                }
+            }
+            cur.z = zn;
+            skip_z = -1;
+            continue;
+        }
+        // the current line is finished (or paused): start the next new ray of
+        // the innermost frame, or resume the line that created them
+        if (depth == 0) break;
+        const int fi = depth - 1;
+        OctFrame &f = fr[fi];
+        const int nxt = f.next;
+        const int nkids = f.n_kids;
+        __syncwarp();
+        if (nxt < nkids) {
+            const int4 kd = kids_all[fi * kOctMaxKids + nxt];
+            if (lane == 0) f.next = nxt + 1;
+            cur.lam = kd.x; cur.i = kd.y; cur.j = kd.z; cur.z = (long long)(unsigned)kd.w;
+            skip_z = -1;
+        } else {
+            cur.lam = f.lam; cur.i = f.i; cur.j = f.j; cur.z = f.z;
+            skip_z = cur.z;
+            depth = fi;
+        }
+        // new rays and the resumed line both start from the frame's snapshot
+        if (V::kNeedI) {
+            const float *src = snap + (size_t)fi * snap_n;
+            for (int q = lane; q < snap_n; q += 32) I[q] = src[q];
+        }
+        __syncwarp();
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(DevModel m, MarchArgs a0,
+                                                                               unsigned *counter)
+{
+    extern __shared__ float smem[];
+    __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
+    float *I = smem + (size_t)wid * a0.per * m.n_ch;
+    float *snap = m.oct_scratch + (size_t)gw * kOctMaxDepth * a0.per * m.n_ch;
+    int4 *kids = m.oct_kids + (size_t)gw * kOctMaxDepth * kOctMaxKids;
+    const long long per_dir = (long long)m.N * m.N;
+    const long long total = per_dir * m.n_dir * a0.n_groups;
+    OctMarchVisitor vis;
+    long long nw = 0;
+    while (true) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if ((long long)it >= total) break;
+        const long long item = (long long)it / a0.n_groups;
+        const MarchArgs a = warp_args(m, a0, (int)((long long)it - item * a0.n_groups));
+        const int dir = (int)(item / per_dir);
+        const long long r = item - (long long)dir * per_dir;
+        OctGeo g;
+        g.D = m.dirs[dir];
+        g.N = m.N;
+        g.Lmax = m.Lmax;
+        g.E = (long long)m.N << kFixedBits;
+        g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
+        oct_traverse<G>(m, a, g, (int)(r / m.N), (int)(r % m.N), I, snap, kids, frames[wid], lane,
+                        vis, nw);
+    }
+    flush_count(m, a0, nw, lane);
+}
+
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(DevModel m, int dir,
+                                                                               OctTraceVisitor vis,
+                                                                               unsigned *counter)
+{
+    __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
+    int4 *kids = m.oct_kids + (size_t)gw * kOctMaxDepth * kOctMaxKids;
+    const long long per_dir = (long long)m.N * m.N;
+    MarchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.per = 1;
+    a.n_groups = 1;
+    a.n_lines = 1;
+    long long nw = 0;
+    OctGeo g;
+    g.D = m.dirs[dir];
+    g.N = m.N;
+    g.Lmax = m.Lmax;
+    g.E = (long long)m.N << kFixedBits;
+    g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
+    while (true) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if ((long long)it >= per_dir) break;
+        oct_traverse<1>(m, a, g, (int)(it / m.N), (int)(it % m.N), nullptr, nullptr, kids, frames[wid],
+                        lane, vis, nw);
+    }
+}
+
+int octree_persistent_warps(const DevModel &m)
+{
+    (void)m;
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    return nsm * kOctBlocksPerSM * kOctWarpsPerBlock;
+}
+
+template <int G>
+static loc_status launch_oct_g(const DevModel &m, const MarchArgs &a, unsigned *counter, cudaStream_t st)
+{
+    const size_t smem = (size_t)kOctWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+    LOC_CUDA_TRY(cudaFuncSetAttribute(march_octree_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
+    march_octree_kernel<G><<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+// counter: one unsigned of device scratch right after the error flag
+loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream_t st)
+{
+    unsigned *counter = (unsigned *)(m.oct_err + 1);
+    LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    switch (a.per) {
+    case 1: return launch_oct_g<1>(m, a, counter, st);
+    case 2: return launch_oct_g<2>(m, a, counter, st);
+    case 3: return launch_oct_g<3>(m, a, counter, st);
+    case 4: return launch_oct_g<4>(m, a, counter, st);
+    case 5: return launch_oct_g<5>(m, a, counter, st);
+    case 6: return launch_oct_g<6>(m, a, counter, st);
+    case 7: return launch_oct_g<7>(m, a, counter, st);
+    case 8: return launch_oct_g<8>(m, a, counter, st);
+    case 9: return launch_oct_g<9>(m, a, counter, st);
+    case 10: return launch_oct_g<10>(m, a, counter, st);
+    case 11: return launch_oct_g<11>(m, a, counter, st);
+    case 12: return launch_oct_g<12>(m, a, counter, st);
+    case 13: return launch_oct_g<13>(m, a, counter, st);
+    case 14: return launch_oct_g<14>(m, a, counter, st);
+    default: return launch_oct_g<15>(m, a, counter, st);
+    }
+}
+
+loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,
+                               unsigned long long *count, cudaStream_t st, unsigned long long *sums)
+{
+    unsigned *counter = (unsigned *)(m.oct_err + 1);
+    LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    LOC_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+    OctTraceVisitor vis;
+    vis.out = out;
+    vis.cap = cap;
+    vis.count = count;
+    vis.sums = sums;
+    vis.dir = dir;
+    const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
+    trace_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, dir, vis, counter);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+}  // namespace loc

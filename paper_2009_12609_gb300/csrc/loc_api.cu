@@ -34,6 +34,8 @@ struct loc_model {
     bool custom_alloc = false;
     std::vector<void *> geo_mem;     // lives as long as the model
     std::vector<void *> mol_mem;     // replaced by loc_set_molecule
+    std::vector<int> oct_child, oct_leaf;       // octree index arrays (host copies)
+    std::vector<double> leaf_f[7];              // octree per-leaf fields (host staging)
     double *sigma_turb = nullptr;    // device copies kept for set_molecule
     double *vx = nullptr, *vy = nullptr, *vz = nullptr;
     bool has_mol = false;
@@ -42,6 +44,8 @@ struct loc_model {
     long long segs_per_sim = 0;
     int n_sm = 152;
     int tuned_per = 0;               // lines per warp chosen by loc_autotune (0: heuristic)
+    size_t oct_scratch_floats = 0;   // octree traversal scratch currently allocated
+    std::vector<void *> oct_mem;
 };
 
 static void *dev_alloc(loc_model *m, size_t bytes, std::vector<void *> &owner)
@@ -155,22 +159,76 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         D.n_dir = d->n_dir;
         D.h0 = d->h0;
     } else if (d->geometry == LOC_OCTREE_3D) {
-        set_error("octree models are not available in this build");
-        return LOC_EINVAL;
+        CHECK(d->n_root >= 1 && d->n_root <= 255, "n_root must be in [1, 255]");
+        CHECK(d->h0 > 0.0 && std::isfinite(d->h0), "h0 must be > 0");
+        CHECK(d->n_dir >= 1 && d->dirs, "3D model needs directions");
+        for (int i = 0; i < d->n_dir; i++) {
+            const double *v = d->dirs + 3 * i;
+            const double n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            CHECK(std::isfinite(n2) && fabs(n2 - 1.0) < 1e-6, "direction %d is not a unit vector", i);
+        }
+        CHECK(d->octree_levels >= 0 && d->octree_levels <= 10, "octree_levels must be in [0, 10]");
+        CHECK(d->octree_refine && d->vx && d->vy && d->vz, "octree model needs refine flags and velocities");
+        const long long N3 = (long long)d->n_root * d->n_root * d->n_root;
+        CHECK(d->octree_n_cells >= N3 && d->octree_n_cells < (1ll << 31), "octree_n_cells out of range");
+        D.N = d->n_root;
+        D.n_dir = d->n_dir;
+        D.h0 = d->h0;
+        D.Lmax = d->octree_levels;
+        D.n_tree = d->octree_n_cells;
+        m->oct_child.assign(D.n_tree, -1);
+        m->oct_leaf.assign(D.n_tree, -1);
+        std::vector<signed char> lev(D.n_tree, 0);
+        long long nxt = N3, nleaf = 0;
+        for (long long c = 0; c < D.n_tree; c++) {
+            const int r = d->octree_refine[c];
+            CHECK(r == 0 || r == 1, "refine flag of cell %lld must be 0 or 1", c);
+            CHECK(c < nxt, "refine flags inconsistent: cell %lld has no parent", c);
+            if (r) {
+                CHECK(lev[c] < D.Lmax, "cell %lld refined below the deepest level", c);
+                CHECK(nxt + 8 <= D.n_tree, "refine flags need more than octree_n_cells cells");
+                m->oct_child[c] = (int)nxt;
+                for (int o = 0; o < 8; o++) lev[nxt + o] = (signed char)(lev[c] + 1);
+                nxt += 8;
+            } else {
+                m->oct_leaf[c] = (int)nleaf++;
+            }
+        }
+        CHECK(nxt == D.n_tree, "refine flags describe %lld cells, octree_n_cells is %lld", nxt, (long long)D.n_tree);
+        nc = nleaf;
+        // per-leaf copies of the per-cell fields (values of refined cells are ignored)
+        auto gather = [&](const double *src, std::vector<double> &dst) {
+            dst.resize(nleaf);
+            for (long long c = 0; c < D.n_tree; c++)
+                if (m->oct_leaf[c] >= 0) dst[m->oct_leaf[c]] = src[c];
+        };
+        CHECK(d->n_h2 && d->t_kin && d->sigma_turb && d->abundance, "per-cell arrays missing");
+        gather(d->n_h2, m->leaf_f[0]);
+        gather(d->t_kin, m->leaf_f[1]);
+        gather(d->sigma_turb, m->leaf_f[2]);
+        gather(d->abundance, m->leaf_f[3]);
+        gather(d->vx, m->leaf_f[4]);
+        gather(d->vy, m->leaf_f[5]);
+        gather(d->vz, m->leaf_f[6]);
     } else {
         CHECK(false, "unknown geometry %d", d->geometry);
     }
     D.n_cells = nc;
-    CHECK(d->n_h2 && d->t_kin && d->sigma_turb && d->abundance, "per-cell arrays missing");
-    CHECK(finite_pos(d->n_h2, nc, true), "n_h2 must be finite and >= 0");
-    CHECK(finite_pos(d->t_kin, nc, false), "t_kin must be finite and > 0");
-    CHECK(finite_pos(d->sigma_turb, nc, true), "sigma_turb must be finite and >= 0");
-    CHECK(finite_pos(d->abundance, nc, true), "abundance must be finite and >= 0");
+    const bool oct = d->geometry == LOC_OCTREE_3D;
+    const double *f_n = oct ? m->leaf_f[0].data() : d->n_h2;
+    const double *f_t = oct ? m->leaf_f[1].data() : d->t_kin;
+    const double *f_s = oct ? m->leaf_f[2].data() : d->sigma_turb;
+    const double *f_a = oct ? m->leaf_f[3].data() : d->abundance;
+    CHECK(f_n && f_t && f_s && f_a, "per-cell arrays missing");
+    CHECK(finite_pos(f_n, nc, true), "n_h2 must be finite and >= 0");
+    CHECK(finite_pos(f_t, nc, false), "t_kin must be finite and > 0");
+    CHECK(finite_pos(f_s, nc, true), "sigma_turb must be finite and >= 0");
+    CHECK(finite_pos(f_a, nc, true), "abundance must be finite and >= 0");
 
-    TRY(upload(m, &D.n_h2, d->n_h2, nc, m->geo_mem, "n_h2"));
-    TRY(upload(m, &D.t_kin, d->t_kin, nc, m->geo_mem, "t_kin"));
-    TRY(upload(m, &D.abundance, d->abundance, nc, m->geo_mem, "abundance"));
-    TRY(upload(m, &m->sigma_turb, d->sigma_turb, nc, m->geo_mem, "sigma_turb"));
+    TRY(upload(m, &D.n_h2, f_n, nc, m->geo_mem, "n_h2"));
+    TRY(upload(m, &D.t_kin, f_t, nc, m->geo_mem, "t_kin"));
+    TRY(upload(m, &D.abundance, f_a, nc, m->geo_mem, "abundance"));
+    TRY(upload(m, &m->sigma_turb, f_s, nc, m->geo_mem, "sigma_turb"));
     TRY(upload<float>(m, &D.inv_s2sig, nullptr, nc, m->geo_mem, "inv_s2sig"));
 
     if (d->geometry == LOC_SHELLS_1D) {
@@ -190,9 +248,21 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         D.n_segs = total;
         m->segs_per_sim = total;
     } else {
-        TRY(upload(m, &m->vx, d->vx, nc, m->geo_mem, "vx"));
-        TRY(upload(m, &m->vy, d->vy, nc, m->geo_mem, "vy"));
-        TRY(upload(m, &m->vz, d->vz, nc, m->geo_mem, "vz"));
+        const double *vx = oct ? m->leaf_f[4].data() : d->vx;
+        const double *vy = oct ? m->leaf_f[5].data() : d->vy;
+        const double *vz = oct ? m->leaf_f[6].data() : d->vz;
+        CHECK(finite_all(vx, nc) && finite_all(vy, nc) && finite_all(vz, nc), "velocities must be finite");
+        TRY(upload(m, &m->vx, vx, nc, m->geo_mem, "vx"));
+        TRY(upload(m, &m->vy, vy, nc, m->geo_mem, "vy"));
+        TRY(upload(m, &m->vz, vz, nc, m->geo_mem, "vz"));
+        if (oct) {
+            TRY(upload(m, &D.child, m->oct_child.data(), D.n_tree, m->geo_mem, "octree children"));
+            TRY(upload(m, &D.leaf_of, m->oct_leaf.data(), D.n_tree, m->geo_mem, "octree leaves"));
+            TRY(upload<int>(m, &D.oct_err, nullptr, 4, m->geo_mem, "octree flags"));
+            LOC_CUDA_TRY(cudaMemsetAsync(D.oct_err, 0, 4 * sizeof(int), m->st));
+            const size_t kid_n = (size_t)octree_persistent_warps(D) * 10 * kOctMaxKids;
+            TRY(upload<int4>(m, &D.oct_kids, nullptr, kid_n, m->geo_mem, "octree frames"));
+        }
         TRY(upload<float4>(m, &D.vel, nullptr, nc, m->geo_mem, "velocity records"));
         double *dirs = nullptr;
         TRY(upload(m, &dirs, d->dirs, 3 * (size_t)d->n_dir, m->geo_mem, "dirs"));
@@ -200,9 +270,19 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         TRY(launch_dir_setup(dirs, d->n_dir, d->h0, D.dirs, m->st));
         unsigned long long *cnt = nullptr, total = 0;
         TRY(upload<unsigned long long>(m, &cnt, nullptr, 1, m->geo_mem, "segment count"));
-        TRY(launch_count3d(D, cnt, m->st));
-        LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
-        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        if (oct) {
+            for (int dd = 0; dd < D.n_dir; dd++) {
+                unsigned long long part = 0;
+                TRY(launch_trace_octree(D, dd, nullptr, 0, cnt, m->st));
+                LOC_CUDA_TRY(cudaMemcpyAsync(&part, cnt, sizeof(part), cudaMemcpyDeviceToHost, m->st));
+                LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+                total += part;
+            }
+        } else {
+            TRY(launch_count3d(D, cnt, m->st));
+            LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
+            LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        }
         m->segs_per_sim = (long long)total;
     }
     LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
@@ -327,6 +407,20 @@ loc_status loc_reset_populations(loc_model *m)
     return LOC_OK;
 }
 
+// octree traversal status flag (set by the kernel when a frame overflows)
+static loc_status octree_status(loc_model *m)
+{
+    if (m->d.geometry != LOC_OCTREE_3D) return LOC_OK;
+    int flag = 0;
+    LOC_CUDA_TRY(cudaMemcpyAsync(&flag, m->d.oct_err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    if (flag) {
+        set_error("octree traversal capacity exceeded (code %d): too many new rays in one cell face", flag);
+        return LOC_ECUDA;
+    }
+    return LOC_OK;
+}
+
 static loc_status check_opts(const loc_iter_opts *o)
 {
     CHECK(o, "NULL options");
@@ -352,6 +446,8 @@ static int lines_per_warp(const loc_model *m, const loc_iter_opts *o)
     if (o->lines_per_pass == 0) {
         const long long items = (D.geometry == LOC_SHELLS_1D) ? (long long)D.n_rays
                                                               : (long long)D.N * D.N * D.n_dir;
+        // octree launches are persistent: enough root lines for every warp
+        (void)0;
         const long long target = 32ll * m->n_sm;
         while (per > 1 && items * ((D.T + per - 1) / per) < target) per = (per + 1) / 2;
     }
@@ -376,6 +472,16 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
     MarchArgs a;
     memset(&a, 0, sizeof(a));
     a.per = lines_per_warp(m, o);
+    if (D.geometry == LOC_OCTREE_3D) {
+        const size_t need = (size_t)octree_persistent_warps(D) * 10 * a.per * D.n_ch;
+        if (need > m->oct_scratch_floats) {
+            LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+            dev_free_all(m, m->oct_mem);
+            D.oct_scratch = (float *)dev_alloc(m, sizeof(float) * need, m->oct_mem);
+            if (!D.oct_scratch) { set_error("device allocation of octree scratch failed"); return LOC_ENOMEM; }
+            m->oct_scratch_floats = need;
+        }
+    }
     a.n_groups = (D.T + a.per - 1) / a.per;
     a.window = (float)o->window_sigmas;
     a.fp64_acc = fp64;
@@ -444,7 +550,7 @@ loc_status loc_march(loc_model *m, const loc_iter_opts *o)
     TRY(launch_line_params(m->d, m->st));
     TRY(march_impl(m, o));
     LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
-    return LOC_OK;
+    return octree_status(m);
 }
 
 loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
@@ -518,6 +624,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     cudaEventDestroy(e1);
     if (st != LOC_OK) return st;
     if (ce != cudaSuccess) { set_error("iteration failed: %s", cudaGetErrorString(ce)); return LOC_ECUDA; }
+    TRY(octree_status(m));
     if (r) {
         memset(r, 0, sizeof(*r));
         r->iterations = it;
@@ -689,6 +796,59 @@ loc_status loc_trace_ray(const loc_model *m, int dir, int64_t i, int64_t j, int6
     return s;
 }
 
+loc_status loc_trace_octree(const loc_model *mc, int dir, int64_t *out7, int64_t cap, int64_t *n_seg)
+{
+    loc_model *m = (loc_model *)mc;
+    if (!m || !n_seg) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (m->d.geometry != LOC_OCTREE_3D) { set_error("loc_trace_octree needs an octree model"); return LOC_EINVAL; }
+    if (dir < 0 || dir >= m->d.n_dir) { set_error("direction %d out of range", dir); return LOC_EINVAL; }
+    if (cap < 0 || (cap > 0 && !out7)) { set_error("bad output buffer"); return LOC_EINVAL; }
+    long long *buf = nullptr;
+    unsigned long long *cnt = nullptr;
+    const long long dcap = cap > 0 ? cap : 1;
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(long long) * 7 * dcap));
+    if (cudaMalloc(&cnt, sizeof(unsigned long long)) != cudaSuccess) { cudaFree(buf); set_error("allocation failed"); return LOC_ENOMEM; }
+    loc_status s = launch_trace_octree(m->d, dir, buf, cap, cnt, m->st);
+    unsigned long long n = 0;
+    if (s == LOC_OK) {
+        cudaError_t e = cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, m->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+        if (e != cudaSuccess) { set_error("trace failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    }
+    if (s == LOC_OK) s = octree_status(m);
+    if (s == LOC_OK) {
+        *n_seg = (int64_t)n;
+        const long long w = ((long long)n < cap) ? (long long)n : cap;
+        if (w > 0) {
+            const cudaError_t e = cudaMemcpy(out7, buf, sizeof(long long) * 7 * w, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+        }
+    }
+    cudaFree(buf);
+    cudaFree(cnt);
+    return s;
+}
+
+loc_status loc_octree_path_sums(const loc_model *mc, int dir, int64_t *out, size_t n_out)
+{
+    loc_model *m = (loc_model *)mc;
+    if (!m || !out) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (m->d.geometry != LOC_OCTREE_3D) { set_error("loc_octree_path_sums needs an octree model"); return LOC_EINVAL; }
+    if (dir < 0 || dir >= m->d.n_dir) { set_error("direction %d out of range", dir); return LOC_EINVAL; }
+    if (n_out < (size_t)m->d.n_cells) { set_error("output needs %lld elements", m->d.n_cells); return LOC_EINVAL; }
+    unsigned long long *buf = nullptr;
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(unsigned long long) * (m->d.n_cells + 1)));
+    loc_status s = LOC_OK;
+    cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(unsigned long long) * (m->d.n_cells + 1), m->st);
+    if (e == cudaSuccess) s = launch_trace_octree(m->d, dir, nullptr, 0, buf + m->d.n_cells, m->st, buf);
+    if (e == cudaSuccess && s == LOC_OK) e = cudaMemcpyAsync(out, buf, sizeof(int64_t) * m->d.n_cells, cudaMemcpyDeviceToHost, m->st);
+    if (e == cudaSuccess && s == LOC_OK) e = cudaStreamSynchronize(m->st);
+    if (e != cudaSuccess) { set_error("path sums failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    cudaFree(buf);
+    if (s == LOC_OK) s = octree_status(m);
+    return s;
+}
+
 loc_status loc_sync(loc_model *m)
 {
     if (!m) { set_error("NULL model"); return LOC_EINVAL; }
@@ -700,6 +860,7 @@ void loc_destroy(loc_model *m)
 {
     if (!m) return;
     cudaStreamSynchronize(m->st);
+    dev_free_all(m, m->oct_mem);
     dev_free_all(m, m->mol_mem);
     dev_free_all(m, m->geo_mem);
     delete m;

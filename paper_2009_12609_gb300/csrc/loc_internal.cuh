@@ -41,6 +41,7 @@ struct Dir3D {
     long long qa, qb;       // slopes in units of 2^-F
     long long Da, ra, Db, rb;       // H 2^F = D q + r (crossing increments)
     long long Qa0, Ra0, Qb0, Rb0;   // first target (H/2) 2^F = Q q + R
+    unsigned long long ma, mb;      // floor((2^64 - 1) / q): division by q
     float d[3];             // true unit direction (for v . d)
     float unit;             // cm per fixed-point unit along the ray
 };
@@ -70,6 +71,15 @@ struct DevModel {
     int N, n_dir;
     double h0;
     Dir3D *dirs;                        // [n_dir]
+
+    // octree (cells level ordered; data arrays above are per leaf)
+    int Lmax;                           // refinement levels below the root
+    long long n_tree;                   // cells of all levels
+    int *child;                         // [n_tree] first child or -1
+    int *leaf_of;                       // [n_tree] leaf index or -1
+    float *oct_scratch;                 // per persistent warp: frame snapshots
+    int4 *oct_kids;                     // per persistent warp: child lines
+    int *oct_err;                       // device flag: frame capacity exceeded
 
     // molecule
     int L, T, P;
@@ -142,6 +152,12 @@ loc_status launch_dir_setup(const double *dirs_dev, int n_dir, double h0, Dir3D 
                             cudaStream_t st);
 loc_status launch_cell_setup(const DevModel &m, const double *sigma_turb, const double *vx,
                              const double *vy, const double *vz, cudaStream_t st);
+loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream_t st);
+loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,
+                               unsigned long long *count, cudaStream_t st,
+                               unsigned long long *sums = nullptr);
+int octree_persistent_warps(const DevModel &m);
+constexpr int kOctMaxKids = 96;         // child lines one frame can hold
 loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,
                              double *norm, cudaStream_t st);
 

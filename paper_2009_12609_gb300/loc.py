@@ -117,7 +117,8 @@ EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecul
            "loc_set_populations", "loc_get_tex", "loc_spectra", "loc_model_info",
            "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
            "loc_radiation1d_noalloc", "loc_autotune", "loc_server_create",
-           "loc_server_submit", "loc_server_poll", "loc_server_stats", "loc_server_destroy"]
+           "loc_server_submit", "loc_server_poll", "loc_server_stats", "loc_server_destroy",
+           "loc_trace_octree", "loc_octree_path_sums"]
 
 
 def library_path():
@@ -153,6 +154,8 @@ def load():
     lib.loc_trace_ray.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                   _i64, _i64, ctypes.c_int64, _i64]
     lib.loc_sync.argtypes = [_vp]
+    lib.loc_trace_octree.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int64, _i64]
+    lib.loc_octree_path_sums.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_size_t]
     lib.loc_destroy.argtypes = [_vp]
     lib.loc_destroy.restype = None
     lib.loc_radiation1d_noalloc.argtypes = [
@@ -232,8 +235,8 @@ def model_desc(model, keep, stream=None, allocator=None):
         d.radius = _pd(keep(_f64(model["radius"])))
         d.n_rays = int(model.get("n_rays", 0) or 0)
         d.v = _pd(keep(_f64(model["v"])))
-    elif geo == "grid3d":
-        d.geometry = LOC_GRID_3D
+    elif geo in ("grid3d", "octree3d"):
+        d.geometry = LOC_GRID_3D if geo == "grid3d" else LOC_OCTREE_3D
         d.n_root = int(model["n_root"])
         d.h0 = float(model["h0"])
         dirs = keep(_f64(model["dirs"]))
@@ -241,6 +244,11 @@ def model_desc(model, keep, stream=None, allocator=None):
         d.dirs = _pd(dirs)
         for key in ("vx", "vy", "vz"):
             setattr(d, key, _pd(keep(_f64(model[key]))))
+        if geo == "octree3d":
+            ref = keep(np.ascontiguousarray(model["refine"], dtype=np.int32))
+            d.octree_levels = int(model["levels"])
+            d.octree_refine = ref.ctypes.data_as(_i32)
+            d.octree_n_cells = len(ref)
     else:
         raise ValueError(f"unknown geometry {geo}")
     d.n_ch = int(model["n_ch"])
@@ -414,6 +422,20 @@ def loc_radiation1d_noalloc(n_shells, n_rays, radius, v_rad, inv_s2sig, n_ch, v_
         float(dv), int(n_lines), ks, nbg, float(window_sigmas), j_ext, beta, stream))
 
 
+def loc_trace_octree(h, d, cap=1 << 22):
+    out = np.zeros((cap, 7), np.int64)
+    n = ctypes.c_int64()
+    _check(load().loc_trace_octree(h, int(d), out.ctypes.data_as(_i64), cap, ctypes.byref(n)))
+    return out[:min(n.value, cap)].copy()
+
+
+def loc_octree_path_sums(h, d):
+    info = loc_model_info(h)
+    out = np.zeros(info["n_cells"], np.int64)
+    _check(load().loc_octree_path_sums(h, int(d), out.ctypes.data_as(_i64), out.size))
+    return out
+
+
 def loc_sync(h):
     _check(load().loc_sync(h))
 
@@ -466,6 +488,12 @@ class Model:
 
     def trace_ray(self, d, i, j, cap=1 << 16):
         return loc_trace_ray(self.h, d, i, j, cap)
+
+    def trace_octree(self, d, cap=1 << 22):
+        return loc_trace_octree(self.h, d, cap)
+
+    def octree_path_sums(self, d):
+        return loc_octree_path_sums(self.h, d)
 
     def sync(self):
         loc_sync(self.h)
