@@ -66,6 +66,14 @@ def workload(name, n_root=128):
         return dict(name=f"3D regular grid {n_root}^3, 12-level rotor (11 lines), 128 channels, "
                          "48 HEALPix directions, 1 ALI iteration",
                     key="grid3d", mol=mol, model=model, n_iter=1, spectra=False)
+    if name == "octree":
+        mol = LI.rotor_molecule()
+        model = LI.octree_cloud()
+        n_leaf = int((model["refine"] == 0).sum())
+        return dict(name=f"3D octree: 64^3 root refined to 5 levels where n > 8x mean "
+                         f"({n_leaf} leaves), 12-level rotor (11 lines), 64 channels, "
+                         "48 HEALPix directions, 1 ALI iteration",
+                    key="octree", mol=mol, model=model, n_iter=1, spectra=False)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -149,6 +157,33 @@ def oracle_sample(wl, budget_s=15.0):
         dt = time.perf_counter() - t0
         ups = segs * nch * T * n / dt
         return ups, cores, f"{n} ALI iteration(s) of the full model ({segs} ray steps x {nch} channels x {T} lines each)"
+    if model["geometry"] == "octree3d":
+        # the oracle walks every lattice line of a direction: sample a small
+        # octree of the same recipe (16^3 root, 3 levels), one direction
+        small = LI.small_octree(N=16, levels=3, refine_frac=0.15, nside=2, n_ch=nch,
+                                box_pc=0.25, abundance=1e-6, seed=5)
+        small["dirs"] = small["dirs"][:1].copy()
+        lm = oracle.leaf_model(small)
+        x = oracle.lte_populations(mol, lm["t_kin"])
+        Kp, S = oracle.line_params(mol, lm, x)
+        nseg = int(sum((oracle.octree_path_sums(small, small["dirs"][0]) > 0).sum() for _ in [0]))
+        t0 = time.perf_counter()
+        oracle.march_octree(mol, small, Kp, S)
+        dt = time.perf_counter() - t0
+        # count active segments of that direction for the update rate
+        N0, Lm = small["n_root"], small["levels"]
+        act = 0
+        for lam in range(Lm + 1):
+            M = N0 << lam
+            for i in range(M):
+                for j in range(M):
+                    if lam and i % 2 == 0 and j % 2 == 0:
+                        continue
+                    sg = oracle.octree_line_segments(small, small["dirs"][0], lam, i, j)
+                    act += int(sg[:, 4].sum())
+        ups = act * nch * T / dt
+        return ups, cores, (f"ray march of one direction on a 16^3-root, 3-level octree of the same "
+                            f"recipe ({act} active ray steps x {nch} channels x {T} lines)")
     # 3D: one direction, a strided subset of root rays
     N = model["n_root"]
     stride = 64
@@ -289,7 +324,8 @@ def run_gpu(args, wl):
     hbm_achieved = seg * bytes_per_seg / per_launch_s / 1e9       # algorithmic GB/s
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupd/s",
                 "frac": achieved / alu_peak, "traffic": None,
-                "kernel": "march1d_kernel" if is1d else "march3d_kernel",
+                "kernel": "march1d_kernel" if is1d else (
+                    "march_octree_kernel" if model["geometry"] == "octree3d" else "march3d_kernel"),
                 "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / 10 ops per update",
                 "hbm_algorithmic_gbs": hbm_achieved,
                 "hbm_frac_of_measured": hbm_achieved / float(peaks["hbm_gbs"]),
@@ -443,7 +479,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rotor1d",
-                    choices=["rotor1d", "twolevel1d", "grid3d", "serve"])
+                    choices=["rotor1d", "twolevel1d", "grid3d", "octree", "serve"])
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the stream")
     ap.add_argument("--open-requests", type=int, default=256, help="serve: open-loop requests")
     ap.add_argument("--baseline-requests", type=int, default=256,

@@ -277,7 +277,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                 st.s = (float)dz * g.D.unit;
                 st.w = (float)dz / (float)HL * wscale;
                 load_lines<G>(m, a, st);
-                nw += march_step<G>(m, a, I, st, lane);
+                nw += (long long)march_step<G>(m, a, I, st, lane) * a.n_lines;
                 __syncwarp();
             } else {
                 if (lane == 0) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
         oct_traverse<G>(m, a, g, (int)(r / m.N), (int)(r % m.N), I, snap, kids, frames[wid], lane,
                         vis, nw);
     }
-    flush_count(m, a0, nw, lane);
+    if (a0.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)nw);   // nw counts lines
 }
 
 __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(DevModel m, int dir,
