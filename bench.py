@@ -68,9 +68,9 @@ def workload(name, n_root=128):
                     key="grid3d", mol=mol, model=model, n_iter=1, spectra=False)
     if name == "octree":
         mol = LI.rotor_molecule()
-        model = LI.octree_cloud()
+        model = LI.octree_cloud(N=n_root if n_root != 128 else 64)
         n_leaf = int((model["refine"] == 0).sum())
-        return dict(name=f"3D octree: 64^3 root refined to 5 levels where n > 8x mean "
+        return dict(name=f"3D octree: {model['n_root']}^3 root refined to 5 levels where n > 8x mean "
                          f"({n_leaf} leaves), 12-level rotor (11 lines), 64 channels, "
                          "48 HEALPix directions, 1 ALI iteration",
                     key="octree", mol=mol, model=model, n_iter=1, spectra=False)
@@ -486,7 +486,8 @@ def main():
                     help="serve: requests solved one at a time by the per-model FP64 path")
     ap.add_argument("--slots", type=int, default=256, help="serve: resident models")
     ap.add_argument("--mem-gb", type=int, default=64, help="serve: device memory budget")
-    ap.add_argument("--n-root", type=int, default=128, help="grid3d: cells per side")
+    ap.add_argument("--n-root", type=int, default=128,
+                    help="grid3d: cells per side; octree: root cells per side (default 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
