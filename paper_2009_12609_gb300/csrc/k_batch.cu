@@ -66,6 +66,7 @@ batch_march_kernel(BatchSlot *slots, const int4 *items, const int *n_items, unsi
         a0.per = S->per;
         a0.n_groups = S->n_groups;
         a0.window = window;
+        a0.inv_dv = (float)(1.0 / m.dv);
         a0.fp64_acc = 0;
         a0.count = 0;
         const MarchArgs a = warp_args(m, a0, w.z);
@@ -150,10 +151,17 @@ loc_status batch_launch_iteration(const BatchLaunch &b, cudaStream_t st)
     batch_clear_kernel<<<b.n_slots, 256, 0, st>>>(b.slots, b.n_slots);
     batch_params_kernel<<<b.n_slots, 256, 0, st>>>(b.slots, b.n_slots);
     const unsigned grid = (unsigned)(b.n_sm * b.blocks_per_sm);
+    // the classes run as parallel branches (fork / join through events), so
+    // one class's tail overlaps the others' work
+    LOC_CUDA_TRY(cudaEventRecord(b.fork, st));
 #define LOC_BATCH_LAUNCH(CI)                                                                      \
+    LOC_CUDA_TRY(cudaStreamWaitEvent(b.side[CI], b.fork, 0));                                      \
     batch_march_kernel<kBatchClassG[CI]><<<grid, kWarpsPerBlock * 32,                              \
-                                           sizeof(float) * kWarpsPerBlock * kBatchClassFloats[CI], st>>>( \
-        b.slots, b.items[CI], b.n_items + CI, b.counters + CI, b.window, kBatchClassFloats[CI]);
+                                           sizeof(float) * kWarpsPerBlock * kBatchClassFloats[CI], \
+                                           b.side[CI]>>>(                                          \
+        b.slots, b.items[CI], b.n_items + CI, b.counters + CI, b.window, kBatchClassFloats[CI]);  \
+    LOC_CUDA_TRY(cudaEventRecord(b.join[CI], b.side[CI]));                                         \
+    LOC_CUDA_TRY(cudaStreamWaitEvent(st, b.join[CI], 0));
     LOC_BATCH_LAUNCH(0)
     LOC_BATCH_LAUNCH(1)
     LOC_BATCH_LAUNCH(2)

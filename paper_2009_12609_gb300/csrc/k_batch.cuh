@@ -39,6 +39,8 @@ struct BatchLaunch {
     int *done_out;               // [n_slots] copy of BatchSlot::done
     float window;
     int n_sm, blocks_per_sm;
+    cudaStream_t side[kBatchClasses];        // one branch per line-group class
+    cudaEvent_t fork, join[kBatchClasses];   // fork / join of the branches
 };
 
 loc_status batch_prepare();

@@ -63,53 +63,67 @@ __global__ void geom1d_offsets(DevModel m, int *tan)
     m.ray_off[m.n_rays] = off;
 }
 
-// thread per shell: W_k = sum_j A_j (length of ray j inside shell k)
+// block per shell: W_k = sum_j A_j (length of ray j inside shell k), the
+// rays split over the block's threads and summed by a fixed-order reduction
 __global__ void geom1d_weights(DevModel m, const int *tan, double *W)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x;
     if (k >= m.K) return;
     double acc = 0.0;
-    for (int j = 0; j < m.n_rays; j++) {
+    for (int j = threadIdx.x; j < m.n_rays; j += blockDim.x) {
         const int t = tan[j];
         if (t > k) continue;
         const double p = ray_p(m, j);
         const double s = (t == k) ? sqrt(m.radius[k] * m.radius[k] - p * p) : shell_chord(m, k, p);
         acc += ray_area(m, j) * 2.0 * s;     // two steps per shell
     }
-    W[k] = acc;
+    __shared__ double red[128];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) W[k] = red[0];
 }
 
-// thread per ray: fill the step records
+// block per ray: step q of ray j (0 <= q < 2 (K - t)), all steps in parallel
 __global__ void geom1d_fill(DevModel m, const int *tan, const double *W)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x;
     if (j >= m.n_rays) return;
     const int t = tan[j];
     if (t >= m.K) return;
     const double p = ray_p(m, j);
     const double A = ray_area(m, j);
     Seg1D *out = m.segs + m.ray_off[j];
-    int n = 0;
-    auto put = [&](int k, double s, double cosv) {
+    const int nin = m.K - t;                       // inbound steps K-1 .. t
+    for (int q = threadIdx.x; q < 2 * nin; q += blockDim.x) {
+        int k;
+        double s, cosv;
+        if (q < nin) {                             // inbound: shell K-1-q
+            k = m.K - 1 - q;
+            const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+            s = (k > t) ? zo - sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p) : zo;
+            cosv = -zo / m.radius[k];
+        } else {                                   // outbound: shell t + (q - nin)
+            k = t + (q - nin);
+            const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+            if (k > t) {
+                const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
+                s = zo - zi;
+                cosv = zi / m.radius[k - 1];
+            } else {
+                s = zo;
+                cosv = 0.0;
+            }
+        }
         Seg1D sg;
         sg.cell = k;
         sg.s = (float)s;
         sg.vlos = (float)((double)m.v1d[k] * cosv);
         sg.w = (float)((W[k] > 0.0) ? A * s / W[k] : 0.0);
-        out[n++] = sg;
-    };
-    for (int k = m.K - 1; k > t; k--) {
-        const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
-        const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
-        put(k, zo - zi, -zo / m.radius[k]);
-    }
-    const double zt = sqrt(m.radius[t] * m.radius[t] - p * p);
-    put(t, zt, -zt / m.radius[t]);
-    put(t, zt, 0.0);
-    for (int k = t + 1; k < m.K; k++) {
-        const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
-        const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
-        put(k, zo - zi, zi / m.radius[k - 1]);
+        out[q] = sg;
     }
 }
 
@@ -120,8 +134,8 @@ loc_status launch_geom1d(const DevModel &m, cudaStream_t st)
     LOC_CUDA_TRY(cudaMallocAsync(&tan, sizeof(int) * m.n_rays, st));
     LOC_CUDA_TRY(cudaMallocAsync(&W, sizeof(double) * m.K, st));
     geom1d_offsets<<<1, 1, 0, st>>>(m, tan);
-    geom1d_weights<<<(m.K + 127) / 128, 128, 0, st>>>(m, tan, W);
-    geom1d_fill<<<(m.n_rays + 127) / 128, 128, 0, st>>>(m, tan, W);
+    geom1d_weights<<<m.K, 128, 0, st>>>(m, tan, W);
+    geom1d_fill<<<m.n_rays, 128, 0, st>>>(m, tan, W);
     LOC_CUDA_TRY(cudaGetLastError());
     LOC_CUDA_TRY(cudaFreeAsync(tan, st));
     LOC_CUDA_TRY(cudaFreeAsync(W, st));
@@ -133,8 +147,8 @@ loc_status launch_geom1d(const DevModel &m, cudaStream_t st)
 loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W)
 {
     geom1d_offsets<<<1, 1, 0, st>>>(m, tan);
-    geom1d_weights<<<(m.K + 127) / 128, 128, 0, st>>>(m, tan, W);
-    geom1d_fill<<<(m.n_rays + 127) / 128, 128, 0, st>>>(m, tan, W);
+    geom1d_weights<<<m.K, 128, 0, st>>>(m, tan, W);
+    geom1d_fill<<<m.n_rays, 128, 0, st>>>(m, tan, W);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

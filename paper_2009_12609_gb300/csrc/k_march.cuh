@@ -95,6 +95,84 @@ __device__ __forceinline__ void load_lines(const DevModel &m, const MarchArgs &a
     for (int t = 0; t < G; t++) st.ks[t] = (t < a.n_lines) ? p[t] : make_float2(0.f, 0.f);
 }
 
+// Narrow windows (at most 16 channels): the lanes take (line, channel) pairs,
+// 32 / Wp lines per chunk with Wp the window rounded up to a power of two.
+// The profile is evaluated once per step (lane c holds channel klo + c), the
+// line parameters come from the lane that holds them, and a segmented
+// reduction over each Wp-lane segment leaves line t's sums in the segment's
+// first lane, which adds them to the cell.
+template <int G>
+__device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchArgs &a, float *I,
+                                                 const Step<G> &st, int lane, int klo, int khi,
+                                                 float u0, float db)
+{
+    const int W = khi - klo;
+    if (W <= 0) return 0;
+    int Wp = 1;
+    while (Wp < W) Wp <<= 1;
+    const int P = 32 / Wp;                         // lines per chunk
+    const int nch = m.n_ch;
+    // profile of the window: lane c (c <= W) evaluates the lower edge of
+    // channel klo + c and takes the upper edge from lane c + 1
+    const float b0 = ((float)(klo + lane) + u0) * db;
+    const float e0 = 0.5f * erfcf(fabsf(b0));
+    const float b1 = __shfl_down_sync(kFull, b0, 1);
+    const float e1 = __shfl_down_sync(kFull, e0, 1);
+    const float phi_c = (lane < W) ? ((b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1)))
+                                   : 0.f;
+    // line parameters: lane t holds line t's K s and S
+    float my_k = 1e-20f, my_s = 0.f;
+#pragma unroll
+    for (int t = 0; t < G; t++) {
+        if (lane == t) {
+            float k = st.ks[t].x * st.s;
+            if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
+            my_k = k;
+            my_s = st.ks[t].y;
+        }
+    }
+    const int tl = lane / Wp, kk = lane - tl * Wp;
+    for (int base = 0; base < a.n_lines; base += P) {
+        const int t = base + tl;
+        const bool act = (kk < W) && (t < a.n_lines);
+        const float phi = __shfl_sync(kFull, phi_c, kk);
+        const float Kt = __shfl_sync(kFull, my_k, t < 32 ? t : 0);
+        const float St = __shfl_sync(kFull, my_s, t < 32 ? t : 0);
+        float ps = 0.f, pe = 0.f;
+        if (act) {
+            const float tm = one_minus_exp(Kt * phi);
+            float *ip = I + t * nch + klo + kk;
+            const float iv = *ip;
+            ps = iv * tm;
+            pe = tm;
+            *ip = fmaf(St - iv, tm, iv);
+        }
+        for (int off = Wp >> 1; off > 0; off >>= 1) {
+            ps += __shfl_xor_sync(kFull, ps, off);
+            pe += __shfl_xor_sync(kFull, pe, off);
+        }
+        if (kk == 0 && t < a.n_lines) {
+            const long long o = st.cell * m.T + a.line0 + t;
+            if (a.fp64_acc) {
+                const double f = (double)st.w / (double)Kt;
+                atomicAdd(m.acc64 + 2 * o, f * (double)ps);
+                atomicAdd(m.acc64 + 2 * o + 1, f * (double)pe);
+            } else {
+                const float f = __fdividef(st.w, Kt);
+                atomicAdd(m.acc + o, make_float2(ps * f, pe * f));
+            }
+        }
+    }
+    if (a.do_norm) {
+        const float nrm = warp_sum(phi_c);
+        if (lane == 0) {
+            if (a.fp64_acc) atomicAdd(m.norm64 + st.cell, (double)st.w * (double)nrm);
+            else atomicAdd(m.norm + st.cell, st.w * nrm);
+        }
+    }
+    return W;
+}
+
 // Process one step.  All lanes call it with identical arguments.  Returns
 // the number of channels computed.
 template <int G>
@@ -103,15 +181,16 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
 {
     const int nch = m.n_ch;
     const float dv = (float)m.dv;
-    const float u0 = ((float)m.v_min + st.vlos) / dv;   // channel coordinate offset
-    const float db = dv * st.inv;                        // channel width in b units
+    const float u0 = ((float)m.v_min + st.vlos) * a.inv_dv;   // channel coordinate offset
+    const float db = dv * st.inv;                              // channel width in b units
     int klo = 0, khi = nch;
     if (a.window > 0.f) {
-        const float hw = a.window / (1.41421356f * db);  // window half-width, channels
+        const float hw = __fdividef(a.window, 1.41421356f * db);  // window half-width, channels
         const float cen = -u0;
         klo = (int)fminf(fmaxf(floorf(cen - hw), 0.f), (float)nch);
         khi = (int)fminf(fmaxf(ceilf(cen + hw), 0.f), (float)nch);
     }
+    if (khi - klo <= 16) return march_step_packed<G>(m, a, I, st, lane, klo, khi, u0, db);
     float Ks[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
@@ -125,7 +204,7 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
     // channels in chunks of 31: lane l evaluates the Gaussian tail at the
     // lower edge of channel base + l and takes the upper edge from lane l + 1
     float nrm = 0.f;
-    for (int base = klo; base < khi; base += 31) {
+    auto chunk = [&](int base) {
         const int k = base + lane;
         const float b0 = ((float)k + u0) * db;
         const float e0 = 0.5f * erfcf(fabsf(b0));
@@ -146,6 +225,18 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
                 }
             }
         }
+    };
+    if constexpr (G <= 2) {
+        // few lines per warp: two independent chunks per pass (more ILP on
+        // the latency-bound path of a single long ray)
+        int base = klo;
+        for (; base + 31 < khi; base += 62) {
+            chunk(base);
+            chunk(base + 31);
+        }
+        if (base < khi) chunk(base);
+    } else {
+        for (int base = klo; base < khi; base += 31) chunk(base);
     }
     // lane t < n_lines ends with line t's {SIJ, ESC}; lane 15 with NORM
     float my_sij, my_esc, my_nrm;

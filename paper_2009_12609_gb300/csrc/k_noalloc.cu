@@ -168,6 +168,7 @@ extern "C" loc_status loc_radiation1d_noalloc(int n_shells, int n_rays, const do
     a.per = per;
     a.n_groups = (T + per - 1) / per;
     a.window = (float)window_sigmas;
+    a.inv_dv = (float)(1.0 / dv);
     s = launch_march(m, a, st);
     if (s != LOC_OK) return s;
     noalloc_finalize<<<(K * T + 255) / 256, 256, 0, st>>>(m.acc, m.norm, nbg, K, T, j_ext, beta);

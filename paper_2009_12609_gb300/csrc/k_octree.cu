@@ -190,6 +190,7 @@ struct OctTraceVisitor {
     unsigned long long *count;
     unsigned long long *sums;  // optional per-leaf sum of dz
     int dir;
+    unsigned local;            // active steps of the current family
 };
 
 // Depth-first traversal of the rays created from root line (i, j).
@@ -280,6 +281,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                 nw += (long long)march_step<G>(m, a, I, st, lane) * a.n_lines;
                 __syncwarp();
             } else {
+                vis.local++;
                 if (lane == 0) {
                     if (vis.sums) atomicAdd(vis.sums + leaf, (unsigned long long)dz);
                     const unsigned long long n = atomicAdd(vis.count, 1ull);
@@ -342,8 +344,9 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
         if (lane == 0) it = atomicAdd(counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if ((long long)it >= total) break;
-        const long long item = (long long)it / a0.n_groups;
-        const MarchArgs a = warp_args(m, a0, (int)((long long)it - item * a0.n_groups));
+        const long long fam = (long long)it / a0.n_groups;     // most work first
+        const long long item = m.oct_order ? (long long)m.oct_order[fam] : fam;
+        const MarchArgs a = warp_args(m, a0, (int)((long long)it - fam * a0.n_groups));
         const int dir = (int)(item / per_dir);
         const long long r = item - (long long)dir * per_dir;
         OctGeo g;
@@ -360,7 +363,8 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
 
 __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(DevModel m, int dir,
                                                                                OctTraceVisitor vis,
-                                                                               unsigned *counter)
+                                                                               unsigned *counter,
+                                                                               unsigned *fam_work)
 {
     __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
     const int lane = threadIdx.x & 31;
@@ -385,8 +389,10 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
         if (lane == 0) it = atomicAdd(counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if ((long long)it >= per_dir) break;
+        vis.local = 0;
         oct_traverse<1>(m, a, g, (int)(it / m.N), (int)(it % m.N), nullptr, nullptr, kids, frames[wid],
                         lane, vis, nw);
+        if (fam_work && lane == 0) fam_work[(long long)dir * per_dir + it] = vis.local;
     }
 }
 
@@ -438,7 +444,8 @@ loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream
 }
 
 loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,
-                               unsigned long long *count, cudaStream_t st, unsigned long long *sums)
+                               unsigned long long *count, cudaStream_t st, unsigned long long *sums,
+                               unsigned *fam_work)
 {
     unsigned *counter = (unsigned *)(m.oct_err + 1);
     LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
@@ -450,7 +457,7 @@ loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long 
     vis.sums = sums;
     vis.dir = dir;
     const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
-    trace_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, dir, vis, counter);
+    trace_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, dir, vis, counter, fam_work);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

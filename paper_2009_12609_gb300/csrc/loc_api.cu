@@ -2,6 +2,7 @@
 // ALI iteration loop, result getters.  Argument marshalling, validation and
 // launch sequencing only; every step of the method runs in the kernels of
 // k_geom.cu, k_march.cu and k_se.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -271,13 +272,26 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         unsigned long long *cnt = nullptr, total = 0;
         TRY(upload<unsigned long long>(m, &cnt, nullptr, 1, m->geo_mem, "segment count"));
         if (oct) {
+            // count the active steps of every root-ray family; the march takes
+            // the families in order of decreasing work (fewer idle warps at
+            // the end of a persistent launch)
+            const long long fams = (long long)D.N * D.N * D.n_dir;
+            unsigned *work = nullptr;
+            TRY(upload<unsigned>(m, &work, nullptr, fams, m->geo_mem, "family work"));
             for (int dd = 0; dd < D.n_dir; dd++) {
                 unsigned long long part = 0;
-                TRY(launch_trace_octree(D, dd, nullptr, 0, cnt, m->st));
+                TRY(launch_trace_octree(D, dd, nullptr, 0, cnt, m->st, nullptr, work));
                 LOC_CUDA_TRY(cudaMemcpyAsync(&part, cnt, sizeof(part), cudaMemcpyDeviceToHost, m->st));
                 LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
                 total += part;
             }
+            std::vector<unsigned> wh(fams);
+            LOC_CUDA_TRY(cudaMemcpy(wh.data(), work, sizeof(unsigned) * fams, cudaMemcpyDeviceToHost));
+            std::vector<int> order(fams);
+            for (long long f = 0; f < fams; f++) order[f] = (int)f;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wh[x] > wh[y]; });
+            TRY(upload(m, &D.oct_order, order.data(), fams, m->geo_mem, "family order"));
+            LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
         } else {
             TRY(launch_count3d(D, cnt, m->st));
             LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
@@ -484,6 +498,7 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
     }
     a.n_groups = (D.T + a.per - 1) / a.per;
     a.window = (float)o->window_sigmas;
+    a.inv_dv = (float)(1.0 / D.dv);
     a.fp64_acc = fp64;
     a.count = o->profile;
     TRY(launch_march(D, a, m->st));

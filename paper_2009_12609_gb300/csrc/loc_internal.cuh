@@ -80,6 +80,7 @@ struct DevModel {
     float *oct_scratch;                 // per persistent warp: frame snapshots
     int4 *oct_kids;                     // per persistent warp: child lines
     int *oct_err;                       // device flag: frame capacity exceeded
+    int *oct_order;                     // root-ray families, most work first (or null)
 
     // molecule
     int L, T, P;
@@ -112,6 +113,7 @@ struct MarchArgs {
     int line0;          // first line of the warp's group (set per warp)
     int n_lines;        // lines in the warp's group (set per warp)
     float window;       // window half-width in sigma (0 = all channels)
+    float inv_dv;       // 1 / channel width (s/cm)
     int fp64_acc;       // accumulate in FP64
     int do_norm;        // the warp also accumulates NORM (group 0)
     int count;          // count computed channel updates into upd_count
@@ -155,7 +157,7 @@ loc_status launch_cell_setup(const DevModel &m, const double *sigma_turb, const 
 loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,
                                unsigned long long *count, cudaStream_t st,
-                               unsigned long long *sums = nullptr);
+                               unsigned long long *sums = nullptr, unsigned *fam_work = nullptr);
 int octree_persistent_warps(const DevModel &m);
 constexpr int kOctMaxKids = 96;         // child lines one frame can hold
 loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,

@@ -125,6 +125,8 @@ struct loc_server {
     int *counts_h = nullptr;       // pinned staging of the counts
     cudaGraphExec_t graph = nullptr;
     bool need_capture = true;
+    cudaStream_t side[kBatchClasses] = {};
+    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
     int n_sm = 152;
     size_t mem_used = 0;
 
@@ -223,6 +225,8 @@ static bool capture_graph(loc_server *s)
     b.window = (float)s->opt.window_sigmas;
     b.n_sm = s->n_sm;
     b.blocks_per_sm = 4;
+    for (int c = 0; c < kBatchClasses; c++) { b.side[c] = s->side[c]; b.join[c] = s->join[c]; }
+    b.fork = s->fork;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
     bool ok = true;
@@ -293,10 +297,12 @@ static bool admit(loc_server *s, int si, Request *q)
     if (launch_cell_setup(m, (const double *)(b + a.sigma), nullptr, nullptr, nullptr, s->st) != LOC_OK) return false;
     if (launch_bg(m, s->st) != LOC_OK) return false;
     if (launch_lte(m, s->st) != LOC_OK) return false;
-    // lines per warp: at most 15 and per x n_ch <= 2048 floats of shared memory
-    int per = std::min(q->T, std::min(15, std::max(1, kBatchLineFloats / q->n_ch)));
+    // lines per warp: per x n_ch <= 2048 floats of shared memory, rounded
+    // down to a compiled group size
+    int per_max = std::min(q->T, std::min(15, std::max(1, kBatchLineFloats / q->n_ch)));
     int cls = 0;
-    while (kBatchClassG[cls] < per) cls++;
+    while (cls + 1 < kBatchClasses && kBatchClassG[cls + 1] <= per_max) cls++;
+    const int per = kBatchClassG[cls];
     bs.active = 1;
     bs.done = 0;
     bs.iter = 0;
@@ -458,6 +464,11 @@ loc_status loc_server_create(loc_server **out, const loc_server_opts *o)
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && nsm > 0) s->n_sm = nsm;
     if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) return fail("stream");
     if (batch_prepare() != LOC_OK) return fail("kernel attributes");
+    for (int c = 0; c < kBatchClasses; c++) {
+        if (cudaStreamCreateWithFlags(&s->side[c], cudaStreamNonBlocking) != cudaSuccess) return fail("stream");
+        if (cudaEventCreateWithFlags(&s->join[c], cudaEventDisableTiming) != cudaSuccess) return fail("event");
+    }
+    if (cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess) return fail("event");
     if (cudaMalloc(&s->slots_d, sizeof(BatchSlot) * o->max_slots) != cudaSuccess) return fail("slot table");
     if (cudaMemset(s->slots_d, 0, sizeof(BatchSlot) * o->max_slots) != cudaSuccess) return fail("slot table");
     if (cudaMalloc(&s->done_d, sizeof(int) * o->max_slots) != cudaSuccess) return fail("flags");
@@ -658,6 +669,11 @@ void loc_server_destroy(loc_server *s)
     cudaFree(s->counts_d);
     cudaFreeHost(s->counts_h);
     cudaFree(s->counters_d);
+    for (int c = 0; c < kBatchClasses; c++) {
+        if (s->side[c]) cudaStreamDestroy(s->side[c]);
+        if (s->join[c]) cudaEventDestroy(s->join[c]);
+    }
+    if (s->fork) cudaEventDestroy(s->fork);
     cudaStreamDestroy(s->st);
     delete s;
 }
