@@ -223,6 +223,28 @@ def run_reference(args, wl):
 
 
 # ----------------------------------------------------------------------------
+# replicas across ranks: every rank solves its own copy of the workload; the
+# job's time is the slowest rank's, its work the sum over ranks
+# ----------------------------------------------------------------------------
+def max_over_ranks(x, world, device):
+    """Maximum of a per-rank scalar over all ranks (all_reduce MAX on the
+    process group's device: cuda under NCCL, cpu under gloo)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_throughput(units_per_rank, world, seconds_max):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed by the slowest rank."""
+    return units_per_rank * world / seconds_max
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def _desc_bytes(model, mol):
@@ -295,17 +317,13 @@ def run_gpu(args, wl):
         dist.barrier()
     clocks = clk.stop()
     ms_steps = [a.elapsed_time(b) for a, b in evs]
-    ms_total = sum(ms_steps)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(sum(ms_steps), world, "cuda")
     ms_step = ms_total / args.steps
 
     seg = reps[0]["segments"]
     iters = reps[0]["iterations"]
     upd_step = seg * nch * T * iters                    # nominal updates per step
-    value = upd_step * args.steps * world / (ms_total / 1e3)
+    value = replicas_throughput(upd_step * args.steps, world, ms_total / 1e3)
 
     # dominant kernel: the ray march (CUDA events around every launch, on the
     # launching stream, inside loc_iterate)
@@ -346,12 +364,8 @@ def run_gpu(args, wl):
                 sp = me.spectra(0, p_spec)
                 d2h += sp.nbytes
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_val = upd_step * world / e2e_s if world == 1 else None
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = upd_step * world / float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
+    e2e_val = replicas_throughput(upd_step, world, e2e_s)
 
     per_iter_launches = 3          # line parameters, march, equilibrium
     gpu_launches = args.steps * (iters * per_iter_launches + (3 if wl["spectra"] else 1))
@@ -372,7 +386,7 @@ def run_gpu(args, wl):
                            "lines_per_warp": tuned_per,
                            "parallelism": f"replicas x{world}" if world > 1 else "single",
                            "l2": "flushed (256 MB write) between timed steps"},
-                "computed_updates_per_s": comp * world / (ms_total / 1e3),
+                "computed_updates_per_s": replicas_throughput(comp, world, ms_total / 1e3),
                 "models_per_s": world * 1e3 / ms_step,
                 "kernel_ms_per_step": {"march": march_ms / args.steps, "se": se_ms / args.steps,
                                        "line_params": par_ms / args.steps},
