@@ -40,6 +40,47 @@ import loc_inputs as LI  # noqa: E402
 WINDOW = 8.0        # channel window half-width in sigma (I unchanged to FP32 beyond it)
 
 
+# sources each march kernel is compiled from: a committed DRAM-traffic figure
+# counts only while these files are unchanged since the capture
+MARCH_SOURCES = {
+    "march1d_kernel": ["k_march.cuh", "k_march1d.cu", "loc_internal.cuh"],
+    "march3d_kernel": ["k_march.cuh", "k_march3d.cu", "walk3d.cuh", "loc_internal.cuh"],
+    "march_octree_kernel": ["k_march.cuh", "k_octree.cu", "loc_internal.cuh"],
+}
+
+
+def sources_digest(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for name in MARCH_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2009_12609_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload_key):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload_key` from
+    the committed ncu summary profiles/<kernel>_<workload>_traffic.md, scaled
+    to a full launch there; None when absent or taken on other sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_key}_traffic.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        parts = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(parts) == 2 and parts[0] in ("sources_sha256", "traffic_bytes_per_launch"):
+            vals[parts[0]] = parts[1].strip("`")
+    if vals.get("sources_sha256") != sources_digest(kernel):
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -340,10 +381,14 @@ def run_gpu(args, wl):
     achieved = comp / launches / per_launch_s / 1e9               # computed Gupd/s
     bytes_per_seg = 28 + 24 * T
     hbm_achieved = seg * bytes_per_seg / per_launch_s / 1e9       # algorithmic GB/s
+    kernel = "march1d_kernel" if is1d else (
+        "march_octree_kernel" if model["geometry"] == "octree3d" else "march3d_kernel")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupd/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "kernel": "march1d_kernel" if is1d else (
-                    "march_octree_kernel" if model["geometry"] == "octree3d" else "march3d_kernel"),
+                "frac": achieved / alu_peak,
+                "traffic": committed_traffic(kernel, wl["key"]),
+                "traffic_unit": "DRAM bytes per launch (ncu, cold cache)",
+                "algorithmic_bytes_per_launch": seg * bytes_per_seg,
+                "kernel": kernel,
                 "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / 10 ops per update",
                 "hbm_algorithmic_gbs": hbm_achieved,
                 "hbm_frac_of_measured": hbm_achieved / float(peaks["hbm_gbs"]),
