@@ -44,6 +44,7 @@ WINDOW = 8.0        # channel window half-width in sigma (I unchanged to FP32 be
 # counts only while these files are unchanged since the capture
 MARCH_SOURCES = {
     "march1d_kernel": ["k_march.cuh", "k_march1d.cu", "loc_internal.cuh"],
+    "march1d_runs": ["k_march.cuh", "k_march1d.cu", "loc_internal.cuh"],
     "march3d_kernel": ["k_march.cuh", "k_march3d.cu", "walk3d.cuh", "loc_internal.cuh"],
     "march_octree_kernel": ["k_march.cuh", "k_octree.cu", "loc_internal.cuh"],
 }
@@ -324,7 +325,7 @@ def run_gpu(args, wl):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    tuned_per, tuned_ms = m.autotune(**tune_opts)
+    tuned_per, tuned_chunk, tuned_ms = m.autotune(**tune_opts)
 
     def step(profile=False):
         m.reset()
@@ -381,7 +382,9 @@ def run_gpu(args, wl):
     achieved = comp / launches / per_launch_s / 1e9               # computed Gupd/s
     bytes_per_seg = 28 + 24 * T
     hbm_achieved = seg * bytes_per_seg / per_launch_s / 1e9       # algorithmic GB/s
-    kernel = "march1d_kernel" if is1d else (
+    # 1D rays cut into runs: the march is the affine + scan + run launches
+    runs = is1d and tuned_chunk > 0
+    kernel = ("march1d_runs" if runs else "march1d_kernel") if is1d else (
         "march_octree_kernel" if model["geometry"] == "octree3d" else "march3d_kernel")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupd/s",
                 "frac": achieved / alu_peak,
@@ -395,24 +398,35 @@ def run_gpu(args, wl):
                 "march_ms_per_launch": per_launch_s * 1e3,
                 "share_of_step": march_ms / ms_total if world == 1 else None}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: model creation
+    # (host arrays -> device, geometry), the same solve with the tuned lines
+    # per warp, populations (and spectra) back to the host
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
+    split = {"create_s": 0.0, "solve_s": 0.0, "readback_s": 0.0}
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         with loc.Model(model, mol) as me:
-            me.iterate(**opts)
+            tb = time.perf_counter()
+            me.iterate(lines_per_pass=tuned_per, steps_per_chunk=tuned_chunk, **opts)
+            tc = time.perf_counter()
             x = me.populations()
             d2h = x.nbytes
             if wl["spectra"]:
                 sp = me.spectra(0, p_spec)
                 d2h += sp.nbytes
+            td = time.perf_counter()
+        split["create_s"] += (tb - ta) / e2e_steps
+        split["solve_s"] += (tc - tb) / e2e_steps
+        split["readback_s"] += (td - tc) / e2e_steps
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
     e2e_val = replicas_throughput(upd_step, world, e2e_s)
 
-    per_iter_launches = 3          # line parameters, march, equilibrium
+    # line parameters, march (1D runs: affine, scan, run), equilibrium
+    per_iter_launches = 5 if runs else 3
     gpu_launches = args.steps * (iters * per_iter_launches + (3 if wl["spectra"] else 1))
 
     if rank == 0:
@@ -429,6 +443,7 @@ def run_gpu(args, wl):
                            "ray_steps_per_iteration": seg, "channels": nch, "lines": T,
                            "window_sigmas": WINDOW, "models_per_step": world,
                            "lines_per_warp": tuned_per,
+                           "steps_per_chunk": tuned_chunk,
                            "parallelism": f"replicas x{world}" if world > 1 else "single",
                            "l2": "flushed (256 MB write) between timed steps"},
                 "computed_updates_per_s": replicas_throughput(comp, world, ms_total / 1e3),
@@ -437,7 +452,8 @@ def run_gpu(args, wl):
                                        "line_params": par_ms / args.steps},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "updates/s",
-                        "h2d_bytes_per_step": _desc_bytes(model, mol), "d2h_bytes_per_step": d2h},
+                        "h2d_bytes_per_step": _desc_bytes(model, mol), "d2h_bytes_per_step": d2h,
+                        "seconds_per_step": split},
                 "gpu_launches": gpu_launches, "clocks": clocks,
                 "wall_s_timed": wall, "peak_source": peak_src}
         print(json.dumps(line))

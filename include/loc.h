@@ -143,14 +143,24 @@ typedef struct loc_molecule_desc {
  *  ali            1: accelerated lambda iteration with the diagonal
  *                 operator (Sect. 2); 0: plain lambda iteration.
  *  precision      LOC_FP32_MARCH or LOC_FP64_ACC.
- *  lines_per_pass 0: all lines in one pass of the rays; k > 0: march the
- *                 rays once per group of k lines (the paper's one-line-at-a-
- *                 time mode is k = 1, Sect. 2).
+ *  lines_per_pass 0: automatic (the value chosen by loc_autotune, else all
+ *                 lines per warp, or fewer when the launch would leave
+ *                 SMs idle); k > 0: each warp carries k lines through the
+ *                 rays (the paper's one-line-at-a-time mode is k = 1,
+ *                 Sect. 2).  Results do not depend on it beyond rounding.
  *  window_sigmas  0: update every channel; w > 0: skip channels farther
  *                 than w sigma from the local line centre (Sect. A.2).
  *  profile        1: time every kernel with CUDA events on the model's
  *                 stream and count the channel updates actually computed
  *                 (fills the *_ms and computed_updates report fields).
+ *  steps_per_chunk  1D models only.  0: automatic (the value chosen by
+ *                 loc_autotune, else whole rays when the rays fill the GPU
+ *                 and runs of steps otherwise); c > 0: every ray is cut
+ *                 into runs of c consecutive steps marched by separate
+ *                 warps (each run's intensity map composed first, then the
+ *                 runs' entering intensities by a scan along the ray);
+ *                 c < 0: whole rays, one warp each.  Results equal the
+ *                 whole-ray march up to rounding.  Ignored for 3D models.
  */
 typedef struct loc_iter_opts {
     int max_iter;
@@ -160,6 +170,7 @@ typedef struct loc_iter_opts {
     int lines_per_pass;
     double window_sigmas;
     int profile;
+    int steps_per_chunk;
 } loc_iter_opts;
 
 /* Iteration report. */
@@ -209,14 +220,18 @@ loc_status loc_reset_populations(loc_model *m);
  * loc_get_radiation (for step-by-step checks). */
 loc_status loc_march(loc_model *m, const loc_iter_opts *o);
 
-/* Choose the number of lines each warp carries through the march (the
- * launch shape: more lines per warp share the profile and the walk, fewer
- * give more warps and fewer registers per thread) by timing one ray
- * simulation per candidate with CUDA events on the model's stream; the
- * fastest is used by later calls whose lines_per_pass is 0.  Runs ray
- * simulations with the current populations (overwrites the accumulators).
- * best_per / best_ms (may be NULL) receive the choice and its time. */
-loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, double *best_ms);
+/* Choose the launch shape of the march: the number of lines each warp
+ * carries (more lines per warp share the profile and the walk, fewer give
+ * more warps and fewer registers per thread) and, for 1D models, the run
+ * length steps_per_chunk (whole rays or runs of 128 / 64 / 32 / 16 steps),
+ * by timing one ray simulation per candidate with CUDA events on the
+ * model's stream; the fastest is used by later calls whose lines_per_pass
+ * (steps_per_chunk) is 0.  Runs ray simulations with the current
+ * populations (overwrites the accumulators).  best_per, best_chunk (-1:
+ * whole rays) and best_ms (each may be NULL) receive the choice and its
+ * time. */
+loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int *best_chunk,
+                        double *best_ms);
 
 /* Per-cell accumulators of the last ray simulation, as FP64:
  * sij, esc [n_lines][n_cells] and norm [n_cells] (any may be NULL).

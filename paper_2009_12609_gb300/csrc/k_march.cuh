@@ -95,6 +95,35 @@ __device__ __forceinline__ void load_lines(const DevModel &m, const MarchArgs &a
     for (int t = 0; t < G; t++) st.ks[t] = (t < a.n_lines) ? p[t] : make_float2(0.f, 0.f);
 }
 
+// Channel coordinate offset u0 (the local line centre sits at channel -u0),
+// channel width db in units of sqrt(2) sigma, and the channel range [klo, khi)
+// of the step's window (all channels when the window is 0).
+template <int G>
+__device__ __forceinline__ void step_window(const DevModel &m, const MarchArgs &a, const Step<G> &st,
+                                            float &u0, float &db, int &klo, int &khi)
+{
+    const int nch = m.n_ch;
+    u0 = ((float)m.v_min + st.vlos) * a.inv_dv;
+    db = (float)m.dv * st.inv;
+    klo = 0;
+    khi = nch;
+    if (a.window > 0.f) {
+        const float hw = __fdividef(a.window, 1.41421356f * db);  // window half-width, channels
+        const float cen = -u0;
+        klo = (int)fminf(fmaxf(floorf(cen - hw), 0.f), (float)nch);
+        khi = (int)fminf(fmaxf(ceilf(cen + hw), 0.f), (float)nch);
+    }
+}
+
+// K s of a line on a step, kept at |K s| >= 1e-20 so that (1 - e^-tau) / (K s)
+// stays phi
+__device__ __forceinline__ float step_ks(float K, float s)
+{
+    float k = K * s;
+    if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
+    return k;
+}
+
 // Narrow windows (at most 16 channels): the lanes take (line, channel) pairs,
 // 32 / Wp lines per chunk with Wp the window rounded up to a power of two.
 // The profile is evaluated once per step (lane c holds channel klo + c), the
@@ -125,9 +154,7 @@ __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchA
 #pragma unroll
     for (int t = 0; t < G; t++) {
         if (lane == t) {
-            float k = st.ks[t].x * st.s;
-            if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
-            my_k = k;
+            my_k = step_ks(st.ks[t].x, st.s);
             my_s = st.ks[t].y;
         }
     }
@@ -180,24 +207,14 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
                                           const Step<G> &st, int lane)
 {
     const int nch = m.n_ch;
-    const float dv = (float)m.dv;
-    const float u0 = ((float)m.v_min + st.vlos) * a.inv_dv;   // channel coordinate offset
-    const float db = dv * st.inv;                              // channel width in b units
-    int klo = 0, khi = nch;
-    if (a.window > 0.f) {
-        const float hw = __fdividef(a.window, 1.41421356f * db);  // window half-width, channels
-        const float cen = -u0;
-        klo = (int)fminf(fmaxf(floorf(cen - hw), 0.f), (float)nch);
-        khi = (int)fminf(fmaxf(ceilf(cen + hw), 0.f), (float)nch);
-    }
+    float u0, db;
+    int klo, khi;
+    step_window(m, a, st, u0, db, klo, khi);
     if (khi - klo <= 16) return march_step_packed<G>(m, a, I, st, lane, klo, khi, u0, db);
     float Ks[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
-        float k = st.ks[t].x * st.s;
-        // keep |K s| >= 1e-20 so that (1 - e^-tau) / (K s) stays phi
-        if (fabsf(k) < 1e-20f) k = (k < 0.f) ? -1e-20f : 1e-20f;
-        Ks[t] = k;
+        Ks[t] = step_ks(st.ks[t].x, st.s);
         sij[t] = 0.f;
         esc[t] = 0.f;
     }
@@ -310,19 +327,17 @@ __device__ __forceinline__ MarchArgs warp_args(const DevModel &m, MarchArgs a, i
 }
 
 
-// One 1D ray (equidistant ray j) through all its steps for the warp's line
-// group; step records are fetched 32 at a time (one coalesced load) and
-// broadcast by shuffle, the next step's line data is prefetched.  Returns the
-// number of channels computed.
-template <int G>
-__device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchArgs &a, float *I,
-                                                 int j, int lane)
+// The 1D step records s0 .. s0 + n - 1 in order, each handed to fn (all
+// lanes, identical arguments); records are fetched 32 at a time (one
+// coalesced load) and broadcast by shuffle, the next step's line data is
+// prefetched.  Returns the sum of fn's results.
+template <int G, class F>
+__device__ __forceinline__ long long walk_steps1d(const DevModel &m, const MarchArgs &a, int s0, int n,
+                                                  int lane, F &&fn)
 {
-    init_ray<G>(m, a, I, lane);
-    const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
     if (n <= 0) return 0;
     Seg1D rec = {0, 0.f, 0.f, 0.f};
-    // step q of the ray (0 <= q < n); a new block of 32 records every 32 steps
+    // step q of the run (0 <= q < n); a new block of 32 records every 32 steps
     auto fetch = [&](int q, Step<G> &st) {
         const int r = q & 31;
         if (r == 0 && q + lane < n) rec = m.segs[s0 + q + lane];
@@ -339,11 +354,62 @@ __device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchA
     for (int q = 0; q < n; q++) {
         const bool more = q + 1 < n;
         if (more) fetch(q + 1, nxt);
-        nw += march_step<G>(m, a, I, cur, lane);
+        nw += fn(cur);
         __syncwarp();
         if (more) cur = nxt;
     }
     return nw;
+}
+
+// One 1D ray (equidistant ray j) through all its steps for the warp's line
+// group.  Returns the number of channels computed.
+template <int G>
+__device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchArgs &a, float *I,
+                                                 int j, int lane)
+{
+    init_ray<G>(m, a, I, lane);
+    const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
+    return walk_steps1d<G>(m, a, s0, n, lane,
+                           [&](const Step<G> &st) { return (long long)march_step<G>(m, a, I, st, lane); });
+}
+
+// Eq. 3 on a step without accumulation, applied to the affine map of a run
+// of steps: with I_out = A I_in + B for the steps so far, the step's
+// I <- I + (S - I)(1 - e^-tau) gives A <- A - A t, B <- B + (S - B) t,
+// t = 1 - e^-tau.  The channel window, profile and t are evaluated exactly
+// as in march_step, so the run's map reproduces the sequential march up to
+// rounding.
+template <int G>
+__device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &a, float *A, float *B,
+                                            const Step<G> &st, int lane)
+{
+    const int nch = m.n_ch;
+    float u0, db;
+    int klo, khi;
+    step_window(m, a, st, u0, db, klo, khi);
+    float Ks[G];
+#pragma unroll
+    for (int t = 0; t < G; t++) Ks[t] = step_ks(st.ks[t].x, st.s);
+    for (int base = klo; base < khi; base += 31) {
+        const int k = base + lane;
+        const float b0 = ((float)k + u0) * db;
+        const float e0 = 0.5f * erfcf(fabsf(b0));
+        const float b1 = __shfl_down_sync(kFull, b0, 1);
+        const float e1 = __shfl_down_sync(kFull, e0, 1);
+        if (lane < 31 && k < khi) {
+            const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                if (t < a.n_lines) {
+                    const float tm = one_minus_exp(Ks[t] * phi);
+                    const int o = t * nch + k;
+                    const float av = A[o], bv = B[o];
+                    A[o] = fmaf(-av, tm, av);
+                    B[o] = fmaf(st.ks[t].y - bv, tm, bv);
+                }
+            }
+        }
+    }
 }
 
 }  // namespace loc

@@ -54,6 +54,134 @@ loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st
 }
 
 // ----------------------------------------------------------------------------
+// Rays cut into runs.  A ray's steps are sequential only through the
+// intensity, and one step (Eq. 3) maps every channel's intensity affinely,
+// I <- I e^-tau + S (1 - e^-tau); so a run of consecutive steps maps the
+// intensity entering it to A I_in + B.  Three launches replace the one
+// warp-per-ray march, so that a long ray is worked on by many warps at once:
+//   affine:  per (run, line group) the run's {A, B} per line and channel
+//            (every run except the last of its ray),
+//   scan:    per (ray, line, channel) I_in of each run, from the background
+//            through the runs' maps in ray order (written over A),
+//   march:   per (run, line group) march_step over the run from its I_in,
+//            accumulating SIJ / ESC / NORM exactly as the whole-ray march.
+// ----------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_affine_kernel(DevModel m, MarchArgs a0)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const long long item = (long long)blockIdx.x * kWarpsPerBlock + wid;
+    if (item >= a0.n_chunks * a0.n_groups) return;
+    const long long gc = item / a0.n_groups;
+    const MarchArgs a = warp_args(m, a0, (int)(item - gc * a0.n_groups));
+    const int j = a.chunk_ray[gc];
+    const int c = (int)(gc - a.chunk_off[j]);
+    const int n = m.ray_off[j + 1] - m.ray_off[j];
+    const int q0 = c * a.chunk;
+    if (q0 + a.chunk >= n) return;                 // last run of the ray: map not needed
+    const int nch = m.n_ch;
+    float *A = smem + (size_t)wid * 2 * a.per * nch;
+    float *B = A + a.per * nch;
+    for (int i = lane; i < a.n_lines * nch; i += 32) {
+        A[i] = 1.f;
+        B[i] = 0.f;
+    }
+    __syncwarp();
+    walk_steps1d<G>(m, a, m.ray_off[j] + q0, a.chunk, lane, [&](const Step<G> &st) {
+        affine_step<G>(m, a, A, B, st, lane);
+        return 0ll;
+    });
+    float2 *out = a.ab + ((size_t)gc * m.T + a.line0) * nch;
+    for (int i = lane; i < a.n_lines * nch; i += 32) out[i] = make_float2(A[i], B[i]);
+}
+
+__global__ void march1d_scan_kernel(DevModel m, MarchArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nch = m.n_ch, T = m.T;
+    if (idx >= (long long)m.n_rays * T * nch) return;
+    const int j = (int)(idx / ((long long)T * nch));
+    const int rem = (int)(idx - (long long)j * T * nch);      // t * nch + k
+    const int t = rem / nch;
+    float I = m.nbg[t];
+    const int c0 = a.chunk_off[j], c1 = a.chunk_off[j + 1];
+    for (int c = c0; c < c1; c++) {
+        float2 *p = a.ab + (size_t)c * T * nch + rem;
+        const float2 v = *p;
+        p->x = I;
+        if (c + 1 < c1) I = fmaf(v.x, I, v.y);
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_run_kernel(DevModel m, MarchArgs a0)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const long long item = (long long)blockIdx.x * kWarpsPerBlock + wid;
+    if (item >= a0.n_chunks * a0.n_groups) return;
+    const long long gc = item / a0.n_groups;
+    const MarchArgs a = warp_args(m, a0, (int)(item - gc * a0.n_groups));
+    const int j = a.chunk_ray[gc];
+    const int c = (int)(gc - a.chunk_off[j]);
+    const int n = m.ray_off[j + 1] - m.ray_off[j];
+    const int q0 = c * a.chunk;
+    const int len = min(a.chunk, n - q0);
+    const int nch = m.n_ch;
+    float *I = smem + (size_t)wid * a.per * nch;
+    const float2 *in = a.ab + ((size_t)gc * m.T + a.line0) * nch;
+    for (int i = lane; i < a.n_lines * nch; i += 32) I[i] = in[i].x;
+    __syncwarp();
+    const long long nw = walk_steps1d<G>(m, a, m.ray_off[j] + q0, len, lane, [&](const Step<G> &st) {
+        return (long long)march_step<G>(m, a, I, st, lane);
+    });
+    flush_count(m, a, nw, lane);
+}
+
+template <int G>
+static loc_status launch_chunked_g(const DevModel &m, const MarchArgs &a, cudaStream_t st)
+{
+    const long long items = a.n_chunks * a.n_groups;
+    const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const size_t smem_a = (size_t)kWarpsPerBlock * 2 * a.per * m.n_ch * sizeof(float);
+    const size_t smem_r = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+    LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_affine_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+    LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_run_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
+    march1d_affine_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem_a, st>>>(m, a);
+    LOC_CUDA_TRY(cudaGetLastError());
+    const long long ns = (long long)m.n_rays * m.T * m.n_ch;
+    march1d_scan_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(m, a);
+    LOC_CUDA_TRY(cudaGetLastError());
+    march1d_run_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem_r, st>>>(m, a);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st)
+{
+    switch (a.per) {
+    case 1: return launch_chunked_g<1>(m, a, st);
+    case 2: return launch_chunked_g<2>(m, a, st);
+    case 3: return launch_chunked_g<3>(m, a, st);
+    case 4: return launch_chunked_g<4>(m, a, st);
+    case 5: return launch_chunked_g<5>(m, a, st);
+    case 6: return launch_chunked_g<6>(m, a, st);
+    case 7: return launch_chunked_g<7>(m, a, st);
+    case 8: return launch_chunked_g<8>(m, a, st);
+    case 9: return launch_chunked_g<9>(m, a, st);
+    case 10: return launch_chunked_g<10>(m, a, st);
+    case 11: return launch_chunked_g<11>(m, a, st);
+    case 12: return launch_chunked_g<12>(m, a, st);
+    case 13: return launch_chunked_g<13>(m, a, st);
+    case 14: return launch_chunked_g<14>(m, a, st);
+    default: return launch_chunked_g<15>(m, a, st);
+    }
+}
+
+// ----------------------------------------------------------------------------
 // 1D emergent spectra: one warp per impact parameter, all channels, FP64 path
 // geometry as in the march; tracks dI = I - n_bg so that the brightness
 // T = (h nu / k) dI keeps relative accuracy in the line wings.

@@ -379,20 +379,24 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
     a.n_lines = 1;
     long long nw = 0;
     OctGeo g;
-    g.D = m.dirs[dir];
     g.N = m.N;
     g.Lmax = m.Lmax;
     g.E = (long long)m.N << kFixedBits;
     g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
+    // dir >= 0: the root lines of that direction; dir < 0: of every direction
+    const long long total = dir >= 0 ? per_dir : per_dir * m.n_dir;
     while (true) {
         unsigned it = 0;
         if (lane == 0) it = atomicAdd(counter, 1u);
         it = __shfl_sync(kFull, it, 0);
-        if ((long long)it >= per_dir) break;
+        if ((long long)it >= total) break;
+        const int d = dir >= 0 ? dir : (int)((long long)it / per_dir);
+        const long long r = dir >= 0 ? (long long)it : (long long)it - (long long)d * per_dir;
+        g.D = m.dirs[d];
         vis.local = 0;
-        oct_traverse<1>(m, a, g, (int)(it / m.N), (int)(it % m.N), nullptr, nullptr, kids, frames[wid],
+        oct_traverse<1>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
                         lane, vis, nw);
-        if (fam_work && lane == 0) fam_work[(long long)dir * per_dir + it] = vis.local;
+        if (fam_work && lane == 0) fam_work[(long long)d * per_dir + r] = vis.local;
     }
 }
 

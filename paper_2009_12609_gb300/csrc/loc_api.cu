@@ -45,6 +45,14 @@ struct loc_model {
     long long segs_per_sim = 0;
     int n_sm = 152;
     int tuned_per = 0;               // lines per warp chosen by loc_autotune (0: heuristic)
+    int tuned_chunk = 0;             // 1D run length chosen by loc_autotune (0: heuristic, -1: whole rays)
+    std::vector<int> ray_off_h;      // 1D: first step of each ray (host copy, n_rays + 1)
+    int run_len = 0;                 // 1D: run length of the current run tables (0: none)
+    long long run_n = 0;             // runs in the current tables
+    int *run_off = nullptr, *run_ray = nullptr;
+    float2 *run_ab = nullptr;        // run maps / entering intensities
+    size_t run_ab_bytes = 0;
+    std::vector<void *> run_mem, run_ab_mem;
     size_t oct_scratch_floats = 0;   // octree traversal scratch currently allocated
     std::vector<void *> oct_mem;
 };
@@ -248,6 +256,9 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
         D.n_segs = total;
         m->segs_per_sim = total;
+        m->ray_off_h.resize(D.n_rays + 1);
+        LOC_CUDA_TRY(cudaMemcpy(m->ray_off_h.data(), D.ray_off, sizeof(int) * (D.n_rays + 1),
+                                cudaMemcpyDeviceToHost));
     } else {
         const double *vx = oct ? m->leaf_f[4].data() : d->vx;
         const double *vy = oct ? m->leaf_f[5].data() : d->vy;
@@ -278,13 +289,9 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             const long long fams = (long long)D.N * D.N * D.n_dir;
             unsigned *work = nullptr;
             TRY(upload<unsigned>(m, &work, nullptr, fams, m->geo_mem, "family work"));
-            for (int dd = 0; dd < D.n_dir; dd++) {
-                unsigned long long part = 0;
-                TRY(launch_trace_octree(D, dd, nullptr, 0, cnt, m->st, nullptr, work));
-                LOC_CUDA_TRY(cudaMemcpyAsync(&part, cnt, sizeof(part), cudaMemcpyDeviceToHost, m->st));
-                LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
-                total += part;
-            }
+            TRY(launch_trace_octree(D, -1, nullptr, 0, cnt, m->st, nullptr, work));
+            LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
+            LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
             std::vector<unsigned> wh(fams);
             LOC_CUDA_TRY(cudaMemcpy(wh.data(), work, sizeof(unsigned) * fams, cudaMemcpyDeviceToHost));
             std::vector<int> order(fams);
@@ -460,8 +467,9 @@ static int lines_per_warp(const loc_model *m, const loc_iter_opts *o)
     if (o->lines_per_pass == 0) {
         const long long items = (D.geometry == LOC_SHELLS_1D) ? (long long)D.n_rays
                                                               : (long long)D.N * D.N * D.n_dir;
-        // octree launches are persistent: enough root lines for every warp
-        (void)0;
+        // octree: at most 6 lines share one traversal (measured best on the
+        // 32^3- and 64^3-root clouds; more lines per warp cost occupancy)
+        if (D.geometry == LOC_OCTREE_3D && per > 6) per = (D.T + (D.T + 5) / 6 - 1) / ((D.T + 5) / 6);
         const long long target = 32ll * m->n_sm;
         while (per > 1 && items * ((D.T + per - 1) / per) < target) per = (per + 1) / 2;
     }
@@ -470,8 +478,69 @@ static int lines_per_warp(const loc_model *m, const loc_iter_opts *o)
     return per;
 }
 
-// one ray simulation: zero the accumulators, then one march launch over
-// all (ray, line group) work items
+// 1D run length (steps per run; 0: whole rays): the requested one, the
+// tuned one, or automatically whole rays when the (ray, line group) items
+// fill the GPU, else the longest power-of-two run (>= 16 steps) that gives
+// at least 64 warps per SM
+static int steps_per_run(const loc_model *m, const loc_iter_opts *o, int per)
+{
+    const DevModel &D = m->d;
+    if (D.geometry != LOC_SHELLS_1D) return 0;
+    int c = o->steps_per_chunk != 0 ? o->steps_per_chunk : m->tuned_chunk;
+    if (c < 0) return 0;
+    if (c > 0) return c;
+    const long long groups = (D.T + per - 1) / per;
+    const long long target = 64ll * m->n_sm;
+    if ((long long)D.n_rays * groups >= target) return 0;
+    int longest = 0;
+    for (int j = 0; j < D.n_rays; j++) longest = std::max(longest, m->ray_off_h[j + 1] - m->ray_off_h[j]);
+    int len = 16;
+    for (int cand = 4096; cand >= 16; cand >>= 1) {
+        long long runs = 0;
+        for (int j = 0; j < D.n_rays; j++) runs += (m->ray_off_h[j + 1] - m->ray_off_h[j] + cand - 1) / cand;
+        len = cand;
+        if (runs * groups >= target) break;
+    }
+    return len >= longest ? 0 : len;
+}
+
+// run tables of length len ([n_rays + 1] first run of each ray, [runs] ray
+// of each run) and the run-map buffer [runs][T][n_ch]
+static loc_status ensure_runs(loc_model *m, int len)
+{
+    DevModel &D = m->d;
+    if (m->run_len != len) {
+        std::vector<int> off(D.n_rays + 1, 0), ray;
+        for (int j = 0; j < D.n_rays; j++) {
+            const int nr = (m->ray_off_h[j + 1] - m->ray_off_h[j] + len - 1) / len;
+            for (int c = 0; c < nr; c++) ray.push_back(j);
+            off[j + 1] = off[j] + nr;
+        }
+        if (ray.empty()) ray.push_back(0);
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));   // the old tables may be in use
+        dev_free_all(m, m->run_mem);
+        m->run_len = 0;
+        TRY(upload(m, &m->run_off, off.data(), off.size(), m->run_mem, "run offsets"));
+        TRY(upload(m, &m->run_ray, ray.data(), ray.size(), m->run_mem, "run rays"));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));   // host tables leave scope
+        m->run_len = len;
+        m->run_n = off[D.n_rays];
+    }
+    const size_t need = sizeof(float2) * (size_t)std::max(m->run_n, 1ll) * D.T * D.n_ch;
+    if (need > m->run_ab_bytes) {
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        dev_free_all(m, m->run_ab_mem);
+        m->run_ab_bytes = 0;
+        m->run_ab = (float2 *)dev_alloc(m, need, m->run_ab_mem);
+        if (!m->run_ab) { set_error("device allocation of the run maps (%zu bytes) failed", need); return LOC_ENOMEM; }
+        m->run_ab_bytes = need;
+    }
+    return LOC_OK;
+}
+
+// one ray simulation: zero the accumulators, then the march over all
+// (ray, line group) work items -- one launch, or for 1D rays cut into runs
+// the affine / scan / run launches
 static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
 {
     DevModel &D = m->d;
@@ -486,6 +555,9 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
     MarchArgs a;
     memset(&a, 0, sizeof(a));
     a.per = lines_per_warp(m, o);
+    const int run = steps_per_run(m, o, a.per);
+    // the affine launch keeps two [per][n_ch] arrays per warp in shared memory
+    if (run > 0) while (a.per > 1 && 32ll * a.per * D.n_ch > 200 * 1024) a.per--;
     if (D.geometry == LOC_OCTREE_3D) {
         const size_t need = (size_t)octree_persistent_warps(D) * 10 * a.per * D.n_ch;
         if (need > m->oct_scratch_floats) {
@@ -501,19 +573,31 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
     a.inv_dv = (float)(1.0 / D.dv);
     a.fp64_acc = fp64;
     a.count = o->profile;
-    TRY(launch_march(D, a, m->st));
+    if (run > 0) {
+        TRY(ensure_runs(m, run));
+        a.chunk = run;
+        a.n_chunks = m->run_n;
+        a.chunk_off = m->run_off;
+        a.chunk_ray = m->run_ray;
+        a.ab = m->run_ab;
+        if (a.n_chunks > 0) TRY(launch_march1d_chunked(D, a, m->st));
+    } else {
+        TRY(launch_march(D, a, m->st));
+    }
     m->has_rad = true;
     m->last_fp64 = fp64;
     return LOC_OK;
 }
 
-loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, double *best_ms)
+loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int *best_chunk,
+                        double *best_ms)
 {
     if (!m) { set_error("NULL model"); return LOC_EINVAL; }
     TRY(check_opts(o));
     if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
     const DevModel &D = m->d;
     m->tuned_per = 0;
+    m->tuned_chunk = 0;
     std::vector<int> cand;
     for (int parts = 1; parts <= D.T; parts++) {
         int per = (D.T + parts - 1) / parts;
@@ -525,34 +609,50 @@ loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, dou
         if (cand.size() >= 6) break;
     }
     if (cand.empty()) cand.push_back(1);
+    // 1D: whole rays (-1) and runs shorter than the longest ray
+    std::vector<int> runs = {-1};
+    if (D.geometry == LOC_SHELLS_1D) {
+        int longest = 0;
+        for (int j = 0; j < D.n_rays; j++) longest = std::max(longest, m->ray_off_h[j + 1] - m->ray_off_h[j]);
+        for (int len : {128, 64, 32, 16})
+            if (len < longest) runs.push_back(len);
+    }
     TRY(launch_line_params(m->d, m->st));
     cudaEvent_t e0, e1;
     LOC_CUDA_TRY(cudaEventCreate(&e0));
     LOC_CUDA_TRY(cudaEventCreate(&e1));
-    int best = cand[0];
+    int best = cand[0], best_run = -1;
     float best_t = 1e30f;
     loc_iter_opts oo = *o;
     loc_status st = LOC_OK;
-    for (int per : cand) {
-        oo.lines_per_pass = per;
-        float t_min = 1e30f;
-        for (int rep = 0; rep < 2 && st == LOC_OK; rep++) {
-            cudaEventRecord(e0, m->st);
-            st = march_impl(m, &oo);
-            cudaEventRecord(e1, m->st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { set_error("autotune march failed"); st = LOC_ECUDA; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < t_min) t_min = ms;
+    for (int run : runs) {
+        for (int per : cand) {
+            // run mode keeps twice the shared memory per warp
+            if (run > 0 && 32ll * per * D.n_ch > 200 * 1024) continue;
+            oo.lines_per_pass = per;
+            oo.steps_per_chunk = run;
+            float t_min = 1e30f;
+            for (int rep = 0; rep < 2 && st == LOC_OK; rep++) {
+                cudaEventRecord(e0, m->st);
+                st = march_impl(m, &oo);
+                cudaEventRecord(e1, m->st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { set_error("autotune march failed"); st = LOC_ECUDA; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < t_min) t_min = ms;
+            }
+            if (st != LOC_OK) break;
+            if (t_min < best_t) { best_t = t_min; best = per; best_run = run; }
         }
         if (st != LOC_OK) break;
-        if (t_min < best_t) { best_t = t_min; best = per; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LOC_OK) return st;
     m->tuned_per = best;
+    m->tuned_chunk = best_run;
     if (best_per) *best_per = best;
+    if (best_chunk) *best_chunk = best_run;
     if (best_ms) *best_ms = best_t;
     return LOC_OK;
 }
@@ -876,6 +976,8 @@ void loc_destroy(loc_model *m)
     if (!m) return;
     cudaStreamSynchronize(m->st);
     dev_free_all(m, m->oct_mem);
+    dev_free_all(m, m->run_mem);
+    dev_free_all(m, m->run_ab_mem);
     dev_free_all(m, m->mol_mem);
     dev_free_all(m, m->geo_mem);
     delete m;

@@ -117,6 +117,13 @@ struct MarchArgs {
     int fp64_acc;       // accumulate in FP64
     int do_norm;        // the warp also accumulates NORM (group 0)
     int count;          // count computed channel updates into upd_count
+    // 1D rays cut into runs of `chunk` consecutive steps (0: whole rays);
+    // see march1d_affine_kernel
+    int chunk;
+    long long n_chunks;     // runs over all rays
+    const int *chunk_off;   // [n_rays + 1] first run of each ray
+    const int *chunk_ray;   // [n_chunks] ray of each run
+    float2 *ab;             // [n_chunks][T][n_ch] run maps {alpha, beta}, then {I_in, -}
 };
 
 // ----------------------------------------------------------------------------
@@ -139,6 +146,7 @@ loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, d
 loc_status launch_line_params(const DevModel &m, cudaStream_t st);
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
+loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);
 loc_status launch_lte(const DevModel &m, cudaStream_t st);

@@ -70,7 +70,7 @@ class loc_iter_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_tex", ctypes.c_double),
                 ("ali", ctypes.c_int), ("precision", ctypes.c_int),
                 ("lines_per_pass", ctypes.c_int), ("window_sigmas", ctypes.c_double),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("steps_per_chunk", ctypes.c_int)]
 
 
 class loc_iter_report(ctypes.Structure):
@@ -143,7 +143,7 @@ def load():
     lib.loc_march.argtypes = [_vp, ctypes.POINTER(loc_iter_opts)]
     lib.loc_reset_populations.argtypes = [_vp]
     lib.loc_autotune.argtypes = [_vp, ctypes.POINTER(loc_iter_opts), ctypes.POINTER(ctypes.c_int),
-                                 ctypes.POINTER(ctypes.c_double)]
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.loc_get_radiation.argtypes = [_vp, _d, _d, _d, ctypes.c_size_t, ctypes.c_size_t]
     lib.loc_get_populations.argtypes = [_vp, _d, ctypes.c_size_t]
     lib.loc_set_populations.argtypes = [_vp, _d, ctypes.c_size_t]
@@ -286,10 +286,11 @@ def molecule_desc(mol, keep, n_levels=None):
 
 
 def iter_opts(max_iter=1, tol_tex=0.0, ali=True, precision="fp32", lines_per_pass=0,
-              window_sigmas=0.0, profile=False):
+              window_sigmas=0.0, profile=False, steps_per_chunk=0):
     prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC}[precision]
     return loc_iter_opts(int(max_iter), float(tol_tex), int(bool(ali)), prec,
-                         int(lines_per_pass), float(window_sigmas), int(bool(profile)))
+                         int(lines_per_pass), float(window_sigmas), int(bool(profile)),
+                         int(steps_per_chunk))
 
 
 # --------------------------------------------------------------------------
@@ -342,11 +343,14 @@ def loc_iterate(h, **opts):
 
 
 def loc_autotune(h, **opts):
+    """Returns (lines per warp, steps per chunk (-1: whole rays), ms)."""
     per = ctypes.c_int()
+    chunk = ctypes.c_int()
     ms = ctypes.c_double()
     o = iter_opts(**opts)
-    _check(load().loc_autotune(h, ctypes.byref(o), ctypes.byref(per), ctypes.byref(ms)))
-    return per.value, ms.value
+    _check(load().loc_autotune(h, ctypes.byref(o), ctypes.byref(per), ctypes.byref(chunk),
+                               ctypes.byref(ms)))
+    return per.value, chunk.value, ms.value
 
 
 def loc_reset_populations(h):

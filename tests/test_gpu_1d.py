@@ -101,6 +101,49 @@ def test_rotor_modes_match_oracle(loc, oracle, window, lines_per_pass):
         assert _tex_err(mol, x_ref, m, oracle) < 1e-4
 
 
+@pytest.mark.parametrize("run", [-1, 1, 7, 16, 33])
+@pytest.mark.parametrize("window,precision", [(0.0, "fp32"), (8.0, "fp32"), (8.0, "fp64acc")])
+def test_runs_of_steps_match_oracle(loc, oracle, run, window, precision):
+    """Rays cut into runs of `run` steps (affine map per run, scan along the
+    ray, march from each run's entering intensity) give the whole-ray
+    accumulators: one-step runs, odd lengths that leave a ragged last run,
+    runs longer than the short rays."""
+    mol = LI.rotor_molecule(n_levels=6)
+    model = LI.cloud1d_rotor(K=48, n_ch=80, n_rays=40)
+    with loc.Model(model, mol) as m:
+        m.march(window_sigmas=window, precision=precision, steps_per_chunk=run, lines_per_pass=2)
+        sij, esc, norm = m.radiation()
+    x = oracle.lte_populations(mol, model["t_kin"])
+    Kp, S = oracle.line_params(mol, model, x)
+    rs, re_, rn = oracle.march_1d(mol, model, Kp, S)
+    np.testing.assert_allclose(norm, rn, rtol=2e-5)
+    np.testing.assert_allclose(sij, rs, rtol=2e-5, atol=1e-12 * np.abs(rs).max())
+    np.testing.assert_allclose(esc, re_, rtol=2e-5)
+
+
+def test_runs_full_size_autotuned(loc, oracle):
+    """Full-size rotor cloud with the autotuned launch shape (lines per warp
+    and run length) over 50 iterations with the channel window."""
+    mol = LI.rotor_molecule()
+    model = LI.cloud1d_rotor()
+    with loc.Model(model, mol) as m:
+        per, run, ms = m.autotune(window_sigmas=8.0)
+        assert ms > 0 and (run == -1 or run in (16, 32, 64, 128))
+        m.reset()
+        m.iterate(max_iter=50, window_sigmas=8.0)
+        x_ref, _ = oracle.iterate_1d(mol, model, 50)
+        assert _tex_err(mol, x_ref, m, oracle) < 1e-4
+        # every fixed run length from the same state agrees with whole rays
+        m.reset()
+        m.march(window_sigmas=8.0, steps_per_chunk=-1)
+        ref = m.radiation()
+        for run in (16, 64):
+            m.march(window_sigmas=8.0, steps_per_chunk=run)
+            got = m.radiation()
+            for a, b in zip(got, ref):
+                np.testing.assert_allclose(a, b, rtol=2e-5, atol=1e-12 * np.abs(b).max())
+
+
 def test_lambda_iteration_and_fp64_accumulation(loc, oracle):
     mol = LI.two_level_molecule()
     model = LI.cloud1d_two_level(K=24, abundance=1e-8)

@@ -130,8 +130,8 @@ def test_autotune_choice_keeps_parity(loc, oracle):
     mol = LI.rotor_molecule(n_levels=10)
     g = LI.small_grid3d(N=6, n_ch=40, nside=2)
     with loc.Model(g, mol) as m:
-        per, ms = m.autotune(window_sigmas=8.0)
-        assert 1 <= per <= 9 and ms > 0
+        per, chunk, ms = m.autotune(window_sigmas=8.0)
+        assert 1 <= per <= 9 and chunk == -1 and ms > 0
         m.march(window_sigmas=8.0)
         sij, esc, norm = m.radiation()
     x = oracle.lte_populations(mol, g["t_kin"])
