@@ -325,7 +325,12 @@ def run_gpu(args, wl):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    tuned_per, tuned_chunk, tuned_ms = m.autotune(**tune_opts)
+    if args.lines_per_warp or args.steps_per_chunk:
+        # fixed launch shape (reproducible profiles): no autotuning
+        tuned_per, tuned_chunk = args.lines_per_warp, args.steps_per_chunk
+        opts.update(lines_per_pass=tuned_per, steps_per_chunk=tuned_chunk)
+    else:
+        tuned_per, tuned_chunk, tuned_ms = m.autotune(**tune_opts)
 
     def step(profile=False):
         m.reset()
@@ -410,7 +415,7 @@ def run_gpu(args, wl):
         ta = time.perf_counter()
         with loc.Model(model, mol) as me:
             tb = time.perf_counter()
-            me.iterate(lines_per_pass=tuned_per, steps_per_chunk=tuned_chunk, **opts)
+            me.iterate(**{**opts, "lines_per_pass": tuned_per, "steps_per_chunk": tuned_chunk})
             tc = time.perf_counter()
             x = me.populations()
             d2h = x.nbytes
@@ -563,6 +568,10 @@ def main():
     ap.add_argument("--mem-gb", type=int, default=64, help="serve: device memory budget")
     ap.add_argument("--n-root", type=int, default=128,
                     help="grid3d: cells per side; octree: root cells per side (default 64)")
+    ap.add_argument("--lines-per-warp", type=int, default=0,
+                    help="fixed lines per warp instead of the autotuned one (0: autotune)")
+    ap.add_argument("--steps-per-chunk", type=int, default=0,
+                    help="1D: fixed run length (-1: whole rays) instead of the autotuned one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":

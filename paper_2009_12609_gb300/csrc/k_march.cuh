@@ -41,15 +41,16 @@ __device__ __forceinline__ float chan_phi(float b0, float db)
     return (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
 }
 
-// 1 - e^-tau: series for |tau| < 1/8 (truncation < 1e-9 relative), the
+// 1 - e^-tau: for |tau| < 1/8 the Taylor series tau (1 - tau/2 + tau^2/6 -
+// ... - tau^5/720) in Horner form (truncation < 1e-9 relative), the
 // exponential otherwise; both evaluated, no divergence.
 __device__ __forceinline__ float one_minus_exp(float tau)
 {
-    float p = 1.f - tau * (1.f / 6.f);
-    p = 1.f - tau * (1.f / 5.f) * p;
-    p = 1.f - tau * (1.f / 4.f) * p;
-    p = 1.f - tau * (1.f / 3.f) * p;
-    p = 1.f - tau * 0.5f * p;
+    float p = fmaf(tau, -1.f / 720.f, 1.f / 120.f);
+    p = fmaf(p, tau, -1.f / 24.f);
+    p = fmaf(p, tau, 1.f / 6.f);
+    p = fmaf(p, tau, -0.5f);
+    p = fmaf(p, tau, 1.f);
     const float e = __expf(-tau);
     return (fabsf(tau) < 0.125f) ? tau * p : 1.f - e;
 }
@@ -219,7 +220,9 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
         esc[t] = 0.f;
     }
     // channels in chunks of 31: lane l evaluates the Gaussian tail at the
-    // lower edge of channel base + l and takes the upper edge from lane l + 1
+    // lower edge of channel base + l and takes the upper edge from lane l + 1;
+    // a full group (n_lines == G) runs without per-line predicates
+    const bool full = (a.n_lines == G);
     float nrm = 0.f;
     auto chunk = [&](int base) {
         const int k = base + lane;
@@ -230,15 +233,26 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
         if (lane < 31 && k < khi) {
             const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
             nrm += phi;
+            float *ip = I + k;
+            if (full) {
 #pragma unroll
-            for (int t = 0; t < G; t++) {
-                if (t < a.n_lines) {
+                for (int t = 0; t < G; t++) {
                     const float tm = one_minus_exp(Ks[t] * phi);
-                    float *ip = I + t * nch + k;
-                    const float iv = *ip;
+                    const float iv = ip[t * nch];
                     sij[t] = fmaf(iv, tm, sij[t]);
                     esc[t] += tm;
-                    *ip = fmaf(st.ks[t].y - iv, tm, iv);
+                    ip[t * nch] = fmaf(st.ks[t].y - iv, tm, iv);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < G; t++) {
+                    if (t < a.n_lines) {
+                        const float tm = one_minus_exp(Ks[t] * phi);
+                        const float iv = ip[t * nch];
+                        sij[t] = fmaf(iv, tm, sij[t]);
+                        esc[t] += tm;
+                        ip[t * nch] = fmaf(st.ks[t].y - iv, tm, iv);
+                    }
                 }
             }
         }
@@ -390,6 +404,7 @@ __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &
     float Ks[G];
 #pragma unroll
     for (int t = 0; t < G; t++) Ks[t] = step_ks(st.ks[t].x, st.s);
+    const bool full = (a.n_lines == G);
     for (int base = klo; base < khi; base += 31) {
         const int k = base + lane;
         const float b0 = ((float)k + u0) * db;
@@ -400,7 +415,7 @@ __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &
             const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                if (t < a.n_lines) {
+                if (full || t < a.n_lines) {
                     const float tm = one_minus_exp(Ks[t] * phi);
                     const int o = t * nch + k;
                     const float av = A[o], bv = B[o];
