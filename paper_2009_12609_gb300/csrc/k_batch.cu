@@ -78,11 +78,10 @@ batch_march_kernel(BatchSlot *slots, const int4 *items, const int *n_items, unsi
 __global__ void __launch_bounds__(kSeWarps * 32)
 batch_se_kernel(BatchSlot *slots, const int2 *cells, const int *n_cells, unsigned *counter)
 {
-    constexpr int max_rates = kBatchMaxRates;
     constexpr int W = kBatchSeLmax + 2;
     extern __shared__ double se_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double *M = se_smem + (size_t)wid * (kBatchSeLmax * W + kBatchSeLmax + 2 * max_rates);
+    double *M = se_smem + (size_t)wid * (kBatchSeLmax * W + kBatchSeLmax);
     const int total = *n_cells;
     while (true) {
         unsigned it = 0;
@@ -93,8 +92,7 @@ batch_se_kernel(BatchSlot *slots, const int2 *cells, const int *n_cells, unsigne
         const BatchSlot *S = slots + w.x;
         if (!S->active) continue;
         const DevModel m = S->m;
-        float d = se_warp_cell<kBatchSeLmax>(m, w.y, S->ali, 0, lane, M, M + kBatchSeLmax * W,
-                                             M + kBatchSeLmax * W + kBatchSeLmax);
+        float d = se_seg_cell<kBatchSeLmax, 32>(m, w.y, true, S->ali, 0, lane, M, M + kBatchSeLmax * W);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) d = fmaxf(d, __shfl_xor_sync(kFull, d, off));
         if (lane == 0 && d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(d));
@@ -124,7 +122,7 @@ __global__ void batch_flags_kernel(BatchSlot *slots, int n_slots, int *done_out)
 
 static size_t se_smem_bytes()
 {
-    return sizeof(double) * kSeWarps * (kBatchSeLmax * (kBatchSeLmax + 2) + kBatchSeLmax + 2 * kBatchMaxRates);
+    return sizeof(double) * kSeWarps * (kBatchSeLmax * (kBatchSeLmax + 2) + kBatchSeLmax);
 }
 
 // kernel attributes, set once outside any stream capture

@@ -182,82 +182,111 @@ loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStr
 }
 
 // ----------------------------------------------------------------------------
-// 1D emergent spectra: one warp per impact parameter, all channels, FP64 path
-// geometry as in the march; tracks dI = I - n_bg so that the brightness
-// T = (h nu / k) dI keeps relative accuracy in the line wings.
+// 1D emergent spectra (the final line-of-sight integration, Sect. 2).  Two
+// launches:
+//   spectra1d_geom:  one thread per (impact parameter, step): the step's
+//                    shell, FP64 chord length and entry cosine as in the
+//                    march, reduced to an FP32 record {K s, S - n_bg, u0, db}
+//                    of line t (FP64 work once per step, not per channel);
+//   spectra1d:       one warp per (impact parameter, 31-channel chunk), all
+//                    channels, tracking dI = I - n_bg so that the brightness
+//                    T = (h nu / k) dI keeps relative accuracy in the wings.
 // ----------------------------------------------------------------------------
-__global__ void spectra1d_kernel(DevModel m, int t, const double *pv, int n_p, float *Tout)
+__global__ void spectra1d_geom_kernel(DevModel m, int t, const double *pv, int n_p, float4 *rec,
+                                      int *nsteps)
 {
-    const int lane = threadIdx.x & 31;
-    const int ip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (ip >= n_p) return;
+    const int K = m.K, S2 = 2 * K;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_p * S2) return;
+    const int ip = (int)(idx / S2), st = (int)(idx - (long long)ip * S2);
     const double p = pv[ip];
-    const int nch = m.n_ch;
-    const int K = m.K;
-    constexpr int CMAX = kMaxChannels / 32;
-    float dI[CMAX];
-#pragma unroll
-    for (int i = 0; i < CMAX; i++) dI[i] = 0.f;
-    const float nb = m.nbg[t];
+    // tangent shell: the first shell whose outer radius exceeds p (radii
+    // strictly increasing)
+    int lo = 0, hi = K;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (m.radius[mid] > p) hi = mid;
+        else lo = mid + 1;
+    }
+    const int tsh = lo;
+    const int n = 2 * (K - tsh);
+    if (st == 0) nsteps[ip] = n;
+    if (st >= n) return;
+    int k;
+    double s, cosv;
+    if (st < K - tsh) {                      // inbound: K-1 .. tsh
+        k = K - 1 - st;
+        const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+        if (k > tsh) {
+            const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
+            s = zo - zi;
+        } else {
+            s = zo;
+        }
+        cosv = -zo / m.radius[k];
+    } else {                                 // outbound: tsh .. K-1
+        k = tsh + (st - (K - tsh));
+        const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
+        if (k > tsh) {
+            const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
+            s = zo - zi;
+            cosv = zi / m.radius[k - 1];
+        } else {
+            s = zo;
+            cosv = 0.0;
+        }
+    }
+    const float vlos = (float)((double)m.v1d[k] * cosv);
     const float dv = (float)m.dv;
-    int tsh = 0;
-    while (tsh < K && !(m.radius[tsh] > p)) tsh++;
-    const int nsteps = (tsh < K) ? 2 * (K - tsh) : 0;
-    for (int st = 0; st < nsteps; st++) {
-        int k;
-        double s, cosv;
-        if (st < K - tsh) {                      // inbound: K-1 .. tsh
-            k = K - 1 - st;
-            const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
-            if (k > tsh) {
-                const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
-                s = zo - zi;
-            } else {
-                s = zo;
-            }
-            cosv = -zo / m.radius[k];
-        } else {                                 // outbound: tsh .. K-1
-            k = tsh + (st - (K - tsh));
-            const double zo = sqrt(m.radius[k] * m.radius[k] - p * p);
-            if (k > tsh) {
-                const double zi = sqrt(m.radius[k - 1] * m.radius[k - 1] - p * p);
-                s = zo - zi;
-                cosv = zi / m.radius[k - 1];
-            } else {
-                s = zo;
-                cosv = 0.0;
-            }
-        }
-        const float vlos = (float)((double)m.v1d[k] * cosv);
-        const float inv = m.inv_s2sig[k];
-        const float u0 = ((float)m.v_min + vlos) / dv;
-        const float db = dv * inv;
-        const float2 ks = m.ks[(long long)k * m.T + t];
-        const float Ksv = ks.x * (float)s;
-        const float src = ks.y - nb;
-#pragma unroll
-        for (int i = 0; i < CMAX; i++) {
-            const int ch = i * 32 + lane;
-            if (ch < nch) {
-                const float phi = chan_phi(((float)ch + u0) * db, db);
-                const float tm = one_minus_exp(Ksv * phi);
-                dI[i] = fmaf(src - dI[i], tm, dI[i]);
-            }
-        }
-    }
-    const float T0 = (float)(kH * m.line_nu[t] / kKB);
-#pragma unroll
-    for (int i = 0; i < CMAX; i++) {
-        const int ch = i * 32 + lane;
-        if (ch < nch) Tout[(long long)ip * nch + ch] = T0 * dI[i];
-    }
+    const float2 ks = m.ks[(long long)k * m.T + t];
+    rec[idx] = make_float4(ks.x * (float)s, ks.y - m.nbg[t], ((float)m.v_min + vlos) / dv,
+                           dv * m.inv_s2sig[k]);
 }
 
-loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p,
-                            float *T_dev, cudaStream_t st)
+__global__ void spectra1d_kernel(DevModel m, int t, int n_p, const float4 *rec, const int *nsteps,
+                                 float *Tout)
 {
+    const int lane = threadIdx.x & 31;
+    const int nch = m.n_ch;
+    const int nchunk = (nch + 30) / 31;
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= (long long)n_p * nchunk) return;
+    const int ip = (int)(item / nchunk);
+    const int ch = (int)(item - (long long)ip * nchunk) * 31 + lane;
+    const int n = nsteps[ip];
+    const float4 *r = rec + (size_t)ip * 2 * m.K;
+    float dI = 0.f;
+    for (int b = 0; b < n; b += 32) {
+        const float4 my = (b + lane < n) ? r[b + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int nb = min(32, n - b);
+        for (int q = 0; q < nb; q++) {
+            const float Ksv = __shfl_sync(kFull, my.x, q);
+            const float src = __shfl_sync(kFull, my.y, q);
+            const float u0 = __shfl_sync(kFull, my.z, q);
+            const float db = __shfl_sync(kFull, my.w, q);
+            // lane l: Gaussian tail at the lower edge of channel ch, the upper
+            // edge from lane l + 1
+            const float b0 = ((float)ch + u0) * db;
+            const float e0 = 0.5f * erfcf(fabsf(b0));
+            const float b1 = __shfl_down_sync(kFull, b0, 1);
+            const float e1 = __shfl_down_sync(kFull, e0, 1);
+            const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
+            const float tm = one_minus_exp(Ksv * phi);
+            dI = fmaf(src - dI, tm, dI);
+        }
+    }
+    if (lane < 31 && ch < nch) Tout[(long long)ip * nch + ch] = (float)(kH * m.line_nu[t] / kKB) * dI;
+}
+
+loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p, float4 *rec,
+                            int *nsteps, float *T_dev, cudaStream_t st)
+{
+    const long long ng = (long long)n_p * 2 * m.K;
+    spectra1d_geom_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(m, t, p_dev, n_p, rec, nsteps);
+    LOC_CUDA_TRY(cudaGetLastError());
+    const long long items = (long long)n_p * ((m.n_ch + 30) / 31);
     const int wpb = 4;
-    spectra1d_kernel<<<(n_p + wpb - 1) / wpb, wpb * 32, 0, st>>>(m, t, p_dev, n_p, T_dev);
+    spectra1d_kernel<<<(unsigned)((items + wpb - 1) / wpb), wpb * 32, 0, st>>>(m, t, n_p, rec, nsteps, T_dev);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

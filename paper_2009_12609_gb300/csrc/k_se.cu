@@ -111,13 +111,11 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
             M[l][u] += rd; M[l][l] -= ru;
             M[u][u] -= rd; M[u][l] += ru;
         }
-        const double Tk = m.t_kin[c], nh = m.n_h2[c];
         for (int p = 0; p < m.P; p++) {
             const int u = m.coll_u[p], l = m.coll_l[p];
-            const double rd = nh * m.coll_k[p];
-            const double ru = rd * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / Tk);
-            M[l][u] += rd; M[l][l] -= ru;
-            M[u][u] -= rd; M[u][l] += ru;
+            const double2 cr = coll_rate(m, c, p);
+            M[l][u] += cr.x; M[l][l] -= cr.y;
+            M[u][u] -= cr.x; M[u][l] += cr.y;
         }
         for (int j = 0; j < L; j++) M[0][j] = 1.0;
         M[0][L] = 1.0;
@@ -157,25 +155,30 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
     if ((threadIdx.x & 31) == 0 && my_d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(my_d));
 }
 
-// One warp per cell.  Lanes compute the radiative and collisional rates of
-// the lines and pairs (k, k+32, ...) into shared memory; lane i then adds
-// the rates that touch level i into row i of the matrix in a fixed order
-// (deterministic); elimination runs with lanes over columns, back
-// substitution with one warp sum per row.
+// Small models: one segment of LMAX lanes per cell, 32 / LMAX cells per warp
+// (se_seg_cell in k_se.cuh).  On GB300 an FP64 warp instruction occupies the
+// FP64 pipe for many cycles whatever the number of active lanes, so packing
+// cells into one warp divides the FP64 instructions per cell.
 // at or above this many cells one thread per cell already fills the GPU
 constexpr long long kSeThreadCells = 1ll << 16;
 
 template <int LMAX>
 __global__ void __launch_bounds__(kSeWarps * 32) se_kernel(DevModel m, int ali, int fp64_acc)
 {
+    constexpr int LW = LMAX;                        // lanes per cell
+    constexpr int CPW = 32 / LW;                    // cells per warp
     constexpr int W = LMAX + 2;                     // row stride: L columns + rhs + pad
+    constexpr int SEG = LMAX * W + LMAX;            // doubles per segment
     extern __shared__ double se_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nrate = m.T + m.P;
-    double *M = se_smem + (size_t)wid * (LMAX * W + LMAX + 2 * nrate);
-    const long long c = (long long)blockIdx.x * kSeWarps + wid;
-    float my_d = 0.f;
-    if (c < m.n_cells) my_d = se_warp_cell<LMAX>(m, c, ali, fp64_acc, lane, M, M + LMAX * W, M + LMAX * W + LMAX);
+    const int seg = lane / LW, sl = lane - seg * LW;
+    double *M = se_smem + (size_t)(wid * CPW + seg) * SEG;
+    const long long c0 = ((long long)blockIdx.x * kSeWarps + wid) * CPW;
+    if (c0 >= m.n_cells) return;                    // whole warp
+    long long c = c0 + seg;
+    const bool valid = c < m.n_cells;
+    if (!valid) c = m.n_cells - 1;                  // repeat a real cell, store nothing
+    float my_d = se_seg_cell<LMAX, LW>(m, c, valid, ali, fp64_acc, sl, M, M + LMAX * W);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) my_d = fmaxf(my_d, __shfl_xor_sync(0xffffffffu, my_d, off));
     if (lane == 0 && my_d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(my_d));
@@ -190,9 +193,11 @@ static loc_status launch_se_l(const DevModel &m, int ali, int fp64_acc, cudaStre
         LOC_CUDA_TRY(cudaGetLastError());
         return LOC_OK;
     }
-    const size_t smem = sizeof(double) * kSeWarps * (LMAX * (LMAX + 2) + LMAX + 2 * (m.T + m.P));
+    constexpr int CPW = 32 / LMAX;
+    const size_t smem = sizeof(double) * kSeWarps * CPW * (LMAX * (LMAX + 2) + LMAX);
     LOC_CUDA_TRY(cudaFuncSetAttribute(se_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned nb = (unsigned)((m.n_cells + kSeWarps - 1) / kSeWarps);
+    const long long cells_per_block = (long long)kSeWarps * CPW;
+    const unsigned nb = (unsigned)((m.n_cells + cells_per_block - 1) / cells_per_block);
     se_kernel<LMAX><<<nb, kSeWarps * 32, smem, st>>>(m, ali, fp64_acc);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
@@ -204,6 +209,28 @@ loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st)
     if (m.L <= 8) return launch_se_l<8>(m, ali, fp64_acc, st);
     if (m.L <= 16) return launch_se_l<16>(m, ali, fp64_acc, st);
     return launch_se_l<32>(m, ali, fp64_acc, st);
+}
+
+// Collision rate table of the model (n_H2 and T_kin are fixed): one thread
+// per (cell, pair).
+__global__ void coll_rates_kernel(DevModel m, double2 *out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m.n_cells * m.P) return;
+    const long long c = idx / m.P;
+    const int p = (int)(idx - c * m.P);
+    const int u = m.coll_u[p], l = m.coll_l[p];
+    const double cul = m.n_h2[c] * m.coll_k[p];
+    out[idx] = make_double2(cul, cul * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / m.t_kin[c]));
+}
+
+loc_status launch_coll_rates(const DevModel &m, double2 *out, cudaStream_t st)
+{
+    const long long n = m.n_cells * m.P;
+    if (n == 0) return LOC_OK;
+    coll_rates_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, out);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
 }
 
 __global__ void tex_kernel(DevModel m, int t, double *out)

@@ -8,7 +8,7 @@
 
 namespace loc {
 
-constexpr int kSeWarps = 4;   // warps per block of the warp-per-cell solve
+constexpr int kSeWarps = 4;   // warps per block of the segment-per-cell solve
 
 __device__ __forceinline__ void line_params_one(const DevModel &m, long long idx)
 {
@@ -46,20 +46,45 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// Statistical equilibrium of cell c by one warp; M: LMAX x (LMAX+2) matrix,
-// F: LMAX scratch, R: 2 (T + P) rates, all in shared memory.  Returns this
-// lane's part of the convergence metric (reduce over the warp).
-template <int LMAX>
-__device__ __forceinline__ float se_warp_cell(const DevModel &m, long long c, int ali, int fp64_acc,
-                                              int lane, double *M, double *F, double *R)
+// Collision rates of pair p in cell c: {C_ul, C_lu} with C_ul = n_H2 k_ul and
+// C_lu = C_ul (g_u / g_l) exp(-(E_u - E_l) / T_kin) (detailed balance); from
+// the per-model table when the model has one (T_kin and n_H2 are fixed).
+__device__ __forceinline__ double2 coll_rate(const DevModel &m, long long c, int p)
+{
+    if (m.coll_rates) return m.coll_rates[c * m.P + p];
+    const int u = m.coll_u[p], l = m.coll_l[p];
+    const double cul = m.n_h2[c] * m.coll_k[p];
+    return make_double2(cul, cul * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / m.t_kin[c]));
+}
+
+// Statistical equilibrium of cell c by a segment of LW lanes (LW a power of
+// two <= 32, L <= LMAX <= LW; sl = lane within the segment; every segment of
+// the warp runs the same control flow).  M: L x W matrix (W = LMAX + 2; L
+// columns and the right-hand side), F: LMAX scratch, both in shared memory
+// and owned by the segment.  With valid == false the segment repeats the work
+// of a real cell but stores nothing.  Returns this lane's part of the
+// convergence metric.
+//
+// Balance of level i: sum_j x_j R(j -> i) - x_i sum_j R(i -> j) = 0, i.e.
+// M[i][j] = R(j -> i) off the diagonal and M[i][i] = -sum_j M[j][i].  Each
+// level pair carries at most one line and one collision pair (checked when
+// the molecule is set), so the lanes of one pass write distinct entries: lines
+// first, then collisions, then the diagonal as column sums -- a fixed order.
+// Elimination with partial pivoting runs with lanes over columns; back
+// substitution with lanes over rows, one broadcast per unknown.
+template <int LMAX, int LW>
+__device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, bool valid, int ali,
+                                             int fp64_acc, int sl, double *M, double *F)
 {
     constexpr int W = LMAX + 2;
-    const int nrate = m.T + m.P;
-    float my_d = 0.f;
-    {
-        const int L = m.L;
-        const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
-        for (int t = lane; t < m.T; t += 32) {
+    const int L = m.L;
+    for (int i = sl; i < L * W; i += LW) M[i] = 0.0;
+    __syncwarp();
+    const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
+    const double inv_nrm = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+    for (int b = 0; b < m.T; b += LW) {
+        const int t = b + sl;
+        if (t < m.T) {
             const int u = m.line_u[t], l = m.line_l[t];
             const double A = m.line_A[t];
             const long long o = c * m.T + t;
@@ -68,81 +93,84 @@ __device__ __forceinline__ float se_warp_cell(const DevModel &m, long long c, in
                 double sj, ej;
                 if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
                 else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
-                J = sj / nrm;
-                beta = ej / nrm;
+                J = sj * inv_nrm;
+                beta = ej * inv_nrm;
             } else {
                 J = m.nbg64[t];
                 beta = 1.0;
             }
             if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
-            R[2 * t] = A * (beta + J);                          // u -> l
-            R[2 * t + 1] = (m.g[u] / m.g[l]) * A * J;           // l -> u
+            M[l * W + u] += A * (beta + J);                     // u -> l
+            M[u * W + l] += (m.g[u] / m.g[l]) * A * J;          // l -> u
         }
-        const double Tk = m.t_kin[c], nh = m.n_h2[c];
-        for (int p = lane; p < m.P; p += 32) {
+    }
+    __syncwarp();
+    for (int b = 0; b < m.P; b += LW) {
+        const int p = b + sl;
+        if (p < m.P) {
             const int u = m.coll_u[p], l = m.coll_l[p];
-            const double cul = nh * m.coll_k[p];
-            R[2 * (m.T + p)] = cul;
-            R[2 * (m.T + p) + 1] = cul * (m.g[u] / m.g[l]) * exp(-(m.energy_K[u] - m.energy_K[l]) / Tk);
+            const double2 cr = coll_rate(m, c, p);
+            M[l * W + u] += cr.x;
+            M[u * W + l] += cr.y;
         }
-        for (int i = lane; i < L * W; i += 32) M[i] = 0.0;
-        __syncwarp();
-        // balance of level i: sum_j x_j R(j -> i) - x_i sum_j R(i -> j) = 0
-        if (lane < L) {
-            double *row = M + lane * W;
-            for (int q = 0; q < nrate; q++) {
-                int u, l;
-                if (q < m.T) { u = m.line_u[q]; l = m.line_l[q]; }
-                else { u = m.coll_u[q - m.T]; l = m.coll_l[q - m.T]; }
-                const double rd = R[2 * q], ru = R[2 * q + 1];
-                if (lane == l) { row[u] += rd; row[l] -= ru; }
-                if (lane == u) { row[u] -= rd; row[l] += ru; }
-            }
-        }
-        __syncwarp();
-        for (int j = lane; j <= L; j += 32) M[j] = 1.0;         // row 0: sum(x) = 1
-        __syncwarp();
-        for (int p = 0; p < L; p++) {
-            // pivot: the first row i >= p with the largest |M[i][p]|
-            double v = (lane >= p && lane < L) ? fabs(M[lane * W + p]) : -1.0;
-            int idx = lane;
+    }
+    __syncwarp();
+    for (int j = sl; j < L; j += LW) {
+        double out = 0.0;
+        for (int i = 0; i < L; i++)
+            if (i != j) out += M[i * W + j];
+        M[j * W + j] = -out;
+    }
+    __syncwarp();
+    for (int j = sl; j <= L; j += LW) M[j] = 1.0;               // row 0: sum(x) = 1
+    __syncwarp();
+    double my_inv = 0.0;                                         // lane p: 1 / U[p][p]
+    for (int p = 0; p < L; p++) {
+        // pivot: the first row i >= p with the largest |M[i][p]|
+        double v = (sl >= p && sl < L) ? fabs(M[sl * W + p]) : -1.0;
+        int idx = sl;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-            }
-            if (idx != p) {
-                for (int j = lane; j <= L; j += 32) {
-                    const double tmp = M[p * W + j];
-                    M[p * W + j] = M[idx * W + j];
-                    M[idx * W + j] = tmp;
-                }
-            }
-            __syncwarp();
-            const double inv = 1.0 / M[p * W + p];
-            if (lane > p && lane < L) F[lane] = M[lane * W + p] * inv;
-            __syncwarp();
-            for (int j = p + lane; j <= L; j += 32) {
-                const double pj = M[p * W + j];
-                for (int i = p + 1; i < L; i++) M[i * W + j] -= F[i] * pj;
-            }
-            __syncwarp();
+        for (int off = LW / 2; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
         }
-        double xi = 0.0;
-        for (int i = L - 1; i >= 0; i--) {
-            const double part = warp_sum_d((lane > i && lane < L) ? M[i * W + lane] * xi : 0.0);
-            const double xv = (M[i * W + L] - part) / M[i * W + i];
-            if (lane == i) xi = xv;
+        if (idx != p) {
+            for (int j = p + sl; j <= L; j += LW) {
+                const double tmp = M[p * W + j];
+                M[p * W + j] = M[idx * W + j];
+                M[idx * W + j] = tmp;
+            }
         }
         __syncwarp();
-        if (lane < L) {
-            m.x_new[c * L + lane] = xi;
-            F[lane] = xi;
+        const double inv = 1.0 / M[p * W + p];
+        if (sl == p) my_inv = inv;
+        if (sl > p && sl < L) F[sl] = M[sl * W + p] * inv;
+        __syncwarp();
+        for (int j = p + sl; j <= L; j += LW) {
+            const double pj = M[p * W + j];
+            for (int i = p + 1; i < L; i++) M[i * W + j] -= F[i] * pj;
         }
         __syncwarp();
+    }
+    // back substitution: lane r keeps the reduced right-hand side of row r
+    double rhs = (sl < L) ? M[sl * W + L] : 0.0;
+    double xi = 0.0;
+    for (int i = L - 1; i >= 0; i--) {
+        const double x = __shfl_sync(0xffffffffu, rhs * my_inv, i, LW);
+        if (sl == i) xi = x;
+        if (sl < i) rhs = fma(-M[sl * W + i], x, rhs);
+    }
+    __syncwarp();
+    if (sl < L) {
+        if (valid) m.x_new[c * L + sl] = xi;
+        F[sl] = xi;
+    }
+    __syncwarp();
+    float my_d = 0.f;
+    if (valid) {
         const double *xo = m.x + c * L;
-        for (int t = lane; t < m.T; t += 32) {
+        for (int t = sl; t < m.T; t += LW) {
             if (F[m.line_u[t]] < 1e-6) continue;
             const double a = tex_of(m, t, xo);
             if (a == 0.0) continue;
@@ -150,6 +178,7 @@ __device__ __forceinline__ float se_warp_cell(const DevModel &m, long long c, in
             my_d = fmaxf(my_d, (float)(fabs(b - a) / fabs(a)));
         }
     }
+    __syncwarp();
     return my_d;
 }
 

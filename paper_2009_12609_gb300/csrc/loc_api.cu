@@ -367,6 +367,10 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
         CHECK(u >= 0 && u < L && l >= 0 && l < L && u != l, "collision %d: bad levels", p);
         CHECK(mol->coll_k[p] >= 0.0 && std::isfinite(mol->coll_k[p]), "collision %d: bad rate", p);
     }
+    CHECK(distinct_level_pairs(mol->line_u, mol->line_l, mol->n_lines, L),
+          "two lines join the same pair of levels");
+    CHECK(distinct_level_pairs(mol->coll_u, mol->coll_l, mol->n_coll, L),
+          "two collision entries join the same pair of levels");
     D.L = L;
     D.T = mol->n_lines;
     D.P = mol->n_coll;
@@ -395,6 +399,13 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
     TRY(upload<unsigned int>(m, &D.dtex_bits, nullptr, 1, m->mol_mem, "dtex"));
     TRY(upload<unsigned long long>(m, &D.maser_count, nullptr, 1, m->mol_mem, "maser count"));
     TRY(upload<unsigned long long>(m, &D.upd_count, nullptr, 1, m->mol_mem, "update count"));
+    // collision rates depend only on n_H2 and T_kin: tabulated once when the
+    // table is modest (<= 4M entries), else computed inside every solve
+    D.coll_rates = nullptr;
+    if (D.P > 0 && nc * D.P <= (1ll << 22)) {
+        TRY(upload<double2>(m, &D.coll_rates, nullptr, nc * D.P, m->mol_mem, "collision rates"));
+        TRY(launch_coll_rates(D, D.coll_rates, m->st));
+    }
     TRY(launch_cell_setup(D, m->sigma_turb, m->vx, m->vy, m->vz, m->st));
     TRY(launch_bg(D, m->st));
     TRY(launch_lte(D, m->st));
@@ -845,16 +856,25 @@ loc_status loc_spectra(const loc_model *m, int t, const double *p_cm, int n_p, d
     if (n_out < n) { set_error("output needs %zu elements", n); return LOC_EINVAL; }
     for (int i = 0; i < n_p; i++)
         if (!(p_cm[i] >= 0.0) || !std::isfinite(p_cm[i])) { set_error("impact parameter %d invalid", i); return LOC_EINVAL; }
-    double *pd = nullptr;
-    float *Td = nullptr;
-    LOC_CUDA_TRY(cudaMalloc(&pd, sizeof(double) * n_p));
-    if (cudaMalloc(&Td, sizeof(float) * n) != cudaSuccess) { cudaFree(pd); set_error("allocation failed"); return LOC_ENOMEM; }
+    // temporaries from the model's allocator: impact parameters, per-step
+    // records [n_p][2 K], step counts, brightness
+    loc_model *mm = const_cast<loc_model *>(m);
+    std::vector<void *> tmp_mem;
+    double *pd = (double *)dev_alloc(mm, sizeof(double) * n_p, tmp_mem);
+    float4 *rec = (float4 *)dev_alloc(mm, sizeof(float4) * (size_t)n_p * 2 * m->d.K, tmp_mem);
+    int *nst = (int *)dev_alloc(mm, sizeof(int) * n_p, tmp_mem);
+    float *Td = (float *)dev_alloc(mm, sizeof(float) * n, tmp_mem);
+    if (!pd || !rec || !nst || !Td) {
+        dev_free_all(mm, tmp_mem);
+        set_error("allocation of the spectra buffers failed");
+        return LOC_ENOMEM;
+    }
     std::vector<float> tmp(n);
     loc_status s = LOC_OK;
     cudaError_t e = cudaMemcpyAsync(pd, p_cm, sizeof(double) * n_p, cudaMemcpyHostToDevice, m->st);
     if (e == cudaSuccess) {
         s = launch_line_params(m->d, m->st);
-        if (s == LOC_OK) s = launch_spectra1d(m->d, t, pd, n_p, Td, m->st);
+        if (s == LOC_OK) s = launch_spectra1d(m->d, t, pd, n_p, rec, nst, Td, m->st);
         if (s == LOC_OK) {
             e = cudaMemcpyAsync(tmp.data(), Td, sizeof(float) * n, cudaMemcpyDeviceToHost, m->st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
@@ -862,8 +882,8 @@ loc_status loc_spectra(const loc_model *m, int t, const double *p_cm, int n_p, d
     }
     if (e != cudaSuccess) { set_error("spectra failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
     if (s == LOC_OK) for (size_t i = 0; i < n; i++) T_out[i] = tmp[i];
-    cudaFree(pd);
-    cudaFree(Td);
+    cudaStreamSynchronize(m->st);
+    dev_free_all(mm, tmp_mem);
     return s;
 }
 

@@ -90,6 +90,7 @@ struct DevModel {
     double *line_A, *line_nu;           // [T]
     int *coll_u, *coll_l;               // [P]
     double *coll_k;                     // [P]
+    double2 *coll_rates;                // [n_cells][P] {C_ul, C_lu}, or null: computed in the solve
     float *nbg;                         // [T] background occupation
     double *nbg64;                      // [T]
 
@@ -140,6 +141,20 @@ void set_error(const char *fmt, ...);
         }                                                                         \
     } while (0)
 
+// true when no two of the n level pairs (u[i], l[i]) join the same two
+// levels (in either order); levels in [0, L), L <= kMaxLevels
+inline bool distinct_level_pairs(const int32_t *u, const int32_t *l, int n, int L)
+{
+    bool seen[kMaxLevels * kMaxLevels] = {};
+    for (int i = 0; i < n; i++) {
+        const int a = u[i] < l[i] ? u[i] : l[i], b = u[i] < l[i] ? l[i] : u[i];
+        if (a < 0 || b >= L) return false;
+        if (seen[a * kMaxLevels + b]) return false;
+        seen[a * kMaxLevels + b] = true;
+    }
+    return true;
+}
+
 // kernel launchers (one per translation unit)
 loc_status launch_geom1d(const DevModel &m, cudaStream_t st);
 loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W);
@@ -150,10 +165,11 @@ loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStr
 loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);
 loc_status launch_lte(const DevModel &m, cudaStream_t st);
+loc_status launch_coll_rates(const DevModel &m, double2 *out, cudaStream_t st);
 loc_status launch_bg(const DevModel &m, cudaStream_t st);
 loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st);
-loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p,
-                            float *T_dev, cudaStream_t st);
+loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p, float4 *rec,
+                            int *nsteps, float *T_dev, cudaStream_t st);
 loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,
                           long long *cells, long long *dz, long long cap,
                           long long *n_out, cudaStream_t st);

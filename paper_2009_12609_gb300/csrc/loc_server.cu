@@ -534,6 +534,11 @@ loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_m
             set_error("molecule: bad collision pair %d", p);
             return LOC_EINVAL;
         }
+    if (!distinct_level_pairs(mol->line_u, mol->line_l, T, L) ||
+        !distinct_level_pairs(mol->coll_u, mol->coll_l, P, L)) {
+        set_error("molecule: two lines or two collision entries join the same pair of levels");
+        return LOC_EINVAL;
+    }
     if (o->max_iter < 1 || !(o->tol_tex >= 0.0)) { set_error("options: max_iter >= 1, tol_tex >= 0"); return LOC_EINVAL; }
     Request *q = new (std::nothrow) Request();
     if (!q) { set_error("host allocation failed"); return LOC_ENOMEM; }

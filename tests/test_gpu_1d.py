@@ -213,3 +213,23 @@ def test_invalid_arguments(loc):
             m.tex(5)
         with pytest.raises(loc.LocError):
             m.set_populations(np.zeros(3))
+
+
+def test_duplicate_level_pairs_rejected(loc):
+    """A molecule with two lines (or two collision entries) on the same pair
+    of levels is rejected by loc_set_molecule."""
+    rot = LI.rotor_molecule(n_levels=4)
+    good = LI.cloud1d_two_level(K=4)
+    dup_line = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in rot.items()}
+    dup_line["line_u"] = dup_line["line_u"].copy()
+    dup_line["line_l"] = dup_line["line_l"].copy()
+    dup_line["line_u"][1], dup_line["line_l"][1] = dup_line["line_l"][0], dup_line["line_u"][0]
+    dup_coll = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in rot.items()}
+    dup_coll["coll_u"][1], dup_coll["coll_l"][1] = dup_coll["coll_u"][0], dup_coll["coll_l"][0]
+    with loc.Model(good) as m:
+        for bad in (dup_line, dup_coll):
+            with pytest.raises(loc.LocError) as e:
+                m.set_molecule(bad)
+            assert e.value.status == loc.LOC_EINVAL
+        m.set_molecule(rot)
+        m.iterate(max_iter=1)
