@@ -86,6 +86,51 @@ __device__ __forceinline__ int oct_locate(const DevModel &m, const OctGeo &g, co
     return c;
 }
 
+// Ancestor cache of the last point located by a warp's march: the point and
+// its leaf level (registers, the same in every lane) and the cells of its
+// path from the root (shared memory, path[0..L]).  The next point shares
+// every level whose box holds both points, so its descent restarts from the
+// deepest such ancestor -- usually the parent -- instead of the root.
+struct OctPathCache {
+    long long p[3];
+    int L;                  // -1: empty
+};
+
+__device__ __forceinline__ int oct_locate_cached(const DevModel &m, const OctGeo &g, const long long p[3],
+                                                 int &level, OctPathCache &pc, int *path, int lane)
+{
+    const int F = kFixedBits;
+    const unsigned long long x = (unsigned long long)((p[0] ^ pc.p[0]) | (p[1] ^ pc.p[1]) | (p[2] ^ pc.p[2]));
+    int s;                  // deepest level whose cell holds both points
+    if (pc.L < 0 || (x >> F) != 0) s = -1;
+    else if (x == 0) s = pc.L;
+    else s = min(F - 1 - (63 - __clzll((long long)x)), pc.L);
+    int c, L;
+    if (s < 0) {
+        c = (int)(((p[2] >> F) * g.N + (p[1] >> F)) * g.N + (p[0] >> F));
+        L = 0;
+        if (lane == 0) path[0] = c;
+    } else {
+        c = path[s];
+        L = s;
+    }
+    while (L < g.Lmax) {
+        const int ch = __ldg(m.child + c);
+        if (ch < 0) break;
+        L++;
+        const int sh = F - L;
+        c = ch + (int)(((p[0] >> sh) & 1) | (((p[1] >> sh) & 1) << 1) | (((p[2] >> sh) & 1) << 2));
+        if (lane == 0) path[L] = c;
+    }
+    __syncwarp();
+    pc.p[0] = p[0];
+    pc.p[1] = p[1];
+    pc.p[2] = p[2];
+    pc.L = L;
+    level = L;
+    return c;
+}
+
 // mirrored lower corner of the level-L box containing original coordinate v
 __device__ __forceinline__ long long oct_mlo(const OctGeo &g, int ax, long long v, int L)
 {
@@ -196,8 +241,8 @@ struct OctTraceVisitor {
 // Depth-first traversal of the rays created from root line (i, j).
 template <int G, class V>
 __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo &g, int i, int j,
-                             float *I, float *snap, int4 *kids_all, OctFrame *fr, int lane, V &vis,
-                             long long &nw)
+                             float *I, float *snap, int4 *kids_all, OctFrame *fr, int *path, int lane,
+                             V &vis, long long &nw)
 {
     const long long H0 = 1ll << kFixedBits;
     const int snap_n = a.per * m.n_ch;
@@ -205,6 +250,9 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
     OctLine cur = {0, i, j, 0};
     long long skip_z = -1;          // a resumed line does not create rays twice at one face
     int depth = 0;
+    OctPathCache pc;
+    pc.p[0] = pc.p[1] = pc.p[2] = 0;
+    pc.L = -1;
     if (V::kNeedI) init_ray<G>(m, a, I, lane);
     while (true) {
         bool done_line = cur.z >= g.E;
@@ -216,7 +264,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
             Au = g.o + (long long)cur.i * (H0 >> cur.lam) + fq(g.D.qa, cur.z);
             Bu = g.o + (long long)cur.j * (H0 >> cur.lam) + fq(g.D.qb, cur.z);
             oct_point(g, Au, Bu, cur.z, p);
-            cell = oct_locate(m, g, p, g.Lmax, Lc);
+            cell = oct_locate_cached(m, g, p, Lc, pc, path, lane);
             done_line = Lc < cur.lam;                       // entered a coarser leaf: terminated
         }
         if (!done_line && cur.z != skip_z) {
@@ -329,6 +377,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
 {
     extern __shared__ float smem[];
     __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
+    __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
@@ -355,8 +404,8 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
         g.Lmax = m.Lmax;
         g.E = (long long)m.N << kFixedBits;
         g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
-        oct_traverse<G>(m, a, g, (int)(r / m.N), (int)(r % m.N), I, snap, kids, frames[wid], lane,
-                        vis, nw);
+        oct_traverse<G>(m, a, g, (int)(r / m.N), (int)(r % m.N), I, snap, kids, frames[wid], paths[wid],
+                        lane, vis, nw);
     }
     if (a0.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)nw);   // nw counts lines
 }
@@ -367,6 +416,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
                                                                                unsigned *fam_work)
 {
     __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
+    __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
@@ -395,7 +445,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
         g.D = m.dirs[d];
         vis.local = 0;
         oct_traverse<1>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
-                        lane, vis, nw);
+                        paths[wid], lane, vis, nw);
         if (fam_work && lane == 0) fam_work[(long long)d * per_dir + r] = vis.local;
     }
 }
