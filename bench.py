@@ -430,9 +430,11 @@ def run_gpu(args, wl):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
     e2e_val = replicas_throughput(upd_step, world, e2e_s)
 
-    # line parameters, march (1D runs: affine, scan, run), equilibrium
+    # per iteration: line parameters, march (1D runs: affine, scan, run),
+    # equilibrium; per step: the LTE reset, and for spectra line parameters,
+    # step geometry and the spectrum kernel
     per_iter_launches = 5 if runs else 3
-    gpu_launches = args.steps * (iters * per_iter_launches + (3 if wl["spectra"] else 1))
+    gpu_launches = args.steps * (iters * per_iter_launches + (4 if wl["spectra"] else 1))
 
     if rank == 0:
         cpu = None

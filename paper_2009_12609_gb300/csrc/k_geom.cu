@@ -49,18 +49,39 @@ __device__ __forceinline__ double shell_chord(const DevModel &m, int k, double p
     return zo - zi;
 }
 
-// one thread: tangent shells, per-ray step counts and offsets (prefix sum)
-__global__ void geom1d_offsets(DevModel m, int *tan)
+// one block of kOffThreads threads: tangent shells and per-ray step counts,
+// then offsets by an exclusive prefix sum.  Thread i takes a contiguous range
+// of rays, so the scan is a per-thread sum, a block scan of those sums and a
+// second pass over each range.
+constexpr int kOffThreads = 1024;
+
+__global__ void __launch_bounds__(kOffThreads) geom1d_offsets(DevModel m, int *tan)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int off = 0;
-    for (int j = 0; j < m.n_rays; j++) {
+    __shared__ int part[kOffThreads];
+    const int tid = threadIdx.x;
+    const int per = (m.n_rays + kOffThreads - 1) / kOffThreads;
+    const int j0 = min(m.n_rays, tid * per), j1 = min(m.n_rays, j0 + per);
+    int sum = 0;
+    for (int j = j0; j < j1; j++) {
         const int t = tangent_shell(m, ray_p(m, j));
         tan[j] = t;
+        sum += (t < m.K) ? 2 * (m.K - t) : 0;
+    }
+    part[tid] = sum;
+    __syncthreads();
+    for (int w = 1; w < kOffThreads; w <<= 1) {          // inclusive scan (Hillis-Steele)
+        const int v = (tid >= w) ? part[tid - w] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int off = part[tid] - sum;
+    for (int j = j0; j < j1; j++) {
         m.ray_off[j] = off;
+        const int t = tan[j];
         off += (t < m.K) ? 2 * (m.K - t) : 0;
     }
-    m.ray_off[m.n_rays] = off;
+    if (tid == kOffThreads - 1) m.ray_off[m.n_rays] = part[tid];
 }
 
 // block per shell: W_k = sum_j A_j (length of ray j inside shell k), the
@@ -133,7 +154,7 @@ loc_status launch_geom1d(const DevModel &m, cudaStream_t st)
     double *W = nullptr;
     LOC_CUDA_TRY(cudaMallocAsync(&tan, sizeof(int) * m.n_rays, st));
     LOC_CUDA_TRY(cudaMallocAsync(&W, sizeof(double) * m.K, st));
-    geom1d_offsets<<<1, 1, 0, st>>>(m, tan);
+    geom1d_offsets<<<1, kOffThreads, 0, st>>>(m, tan);
     geom1d_weights<<<m.K, 128, 0, st>>>(m, tan, W);
     geom1d_fill<<<m.n_rays, 128, 0, st>>>(m, tan, W);
     LOC_CUDA_TRY(cudaGetLastError());
@@ -146,7 +167,7 @@ loc_status launch_geom1d(const DevModel &m, cudaStream_t st)
 // doubles) instead of stream-ordered allocations.
 loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W)
 {
-    geom1d_offsets<<<1, 1, 0, st>>>(m, tan);
+    geom1d_offsets<<<1, kOffThreads, 0, st>>>(m, tan);
     geom1d_weights<<<m.K, 128, 0, st>>>(m, tan, W);
     geom1d_fill<<<m.n_rays, 128, 0, st>>>(m, tan, W);
     LOC_CUDA_TRY(cudaGetLastError());
