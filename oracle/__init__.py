@@ -403,3 +403,42 @@ def iterate_octree(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels
         dt[it] = max_rel_dtex(mol, x, xn, n_levels)
         x = xn
     return x, dt
+
+
+def map_3d(mol, model, x, line, d, lam=0, pix_stride=1, F=FIXED_BITS, n_levels=None):
+    """Emergent map of a 3D model (grid or octree) along unit direction d:
+    T_RJ [M * M][n_ch], M = n_root << lam, pixel (i, j) at row i * M + j
+    (i along the direction's first transverse axis, j along the second);
+    x: populations per cell (grid) or per leaf (octree).  Only pixels with
+    index % pix_stride == 0 are computed (others are 0)."""
+    lib = _load()
+    M_ = _Mol(mol, n_levels)
+    N = int(model["n_root"])
+    if model["geometry"] == "octree3d":
+        _, Lmax, refine = _tree_args(model)
+        lf = leaves(model)
+        Kl, Sl = line_params(mol, leaf_model(model), x, n_levels)
+        nc = len(refine)
+        Kp = np.zeros((M_.T, nc))
+        S = np.zeros((M_.T, nc))
+        Kp[:, lf] = Kl
+        S[:, lf] = Sl
+    else:
+        Lmax, nc = 0, N ** 3
+        refine = np.zeros(nc, np.int32)
+        Kp, S = line_params(mol, model, x, n_levels)
+        if lam != 0:
+            raise ValueError("a regular grid has level-0 pixels only")
+    Mp = N << lam
+    T = np.zeros((Mp * Mp, int(model["n_ch"])))
+    lib.lo_map_3d.restype = ctypes.c_int
+    r = lib.lo_map_3d(M_.ref, int(line), N, int(Lmax), int(F), ctypes.c_int64(nc), _p(refine),
+                      ctypes.c_double(model["h0"]), _p(_f64(model["t_kin"])),
+                      _p(_f64(model["sigma_turb"])), _p(_f64(model["vx"])), _p(_f64(model["vy"])),
+                      _p(_f64(model["vz"])), _p(_f64(d)), int(lam), ctypes.c_int64(pix_stride),
+                      int(model["n_ch"]), ctypes.c_double(model["v_min"]),
+                      ctypes.c_double(model["dv"]), ctypes.c_double(model["t_bg"]),
+                      _p(_f64(Kp)), _p(_f64(S)), _p(T))
+    if r != 0:
+        raise ValueError("inconsistent refinement flags")
+    return T

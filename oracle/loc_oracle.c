@@ -1081,6 +1081,63 @@ int lo_march_octree(const lo_molecule *m, int N, int Lmax, int F, int64_t n_cell
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Emergent map of a 3D model (Sect. 2: after convergence the line of sight */
+/* is integrated for chosen transitions; Sect. 3.3 shows such maps).  The   */
+/* map is seen along direction d: one pixel per lattice line (lam, i, j) of */
+/* that direction (i along the first transverse axis a, j along b; M =      */
+/* N << lam pixels per side; lam = 0 for a regular grid).  The pixel's ray  */
+/* starts with the background at the upstream face and crosses the periodic */
+/* model once along the main axis, through every cell it meets -- every     */
+/* leaf of an octree, whatever its level (an observer's line of sight; the  */
+/* activation rules of the ray simulation do not apply) -- with the         */
+/* intensity update of Eq. 3 and no accumulation.  Output, pixels with      */
+/* (i M + j) % pix_stride == 0 (others untouched):                          */
+/*   T[(i M + j) n_ch + k] = (h nu / k) (I_k - n_bg)   for line `line`.     */
+/* A regular grid is the tree with Lmax = 0 and no refined cell.  Per-cell  */
+/* arrays and Kp, S [line][cell] are level ordered over all cells.  Returns */
+/* 0, or -1 for an inconsistent refinement array.                          */
+/* ------------------------------------------------------------------------ */
+int lo_map_3d(const lo_molecule *m, int line, int N, int Lmax, int F, int64_t n_cells,
+              const int32_t *refine, double h0, const double *t_kin, const double *sigma_turb,
+              const double *vx, const double *vy, const double *vz, const double *d, int lam,
+              int64_t pix_stride, int n_ch, double v_min, double dv, double t_bg,
+              const double *Kp, const double *S, double *T)
+{
+    lo_tree t;
+    if (lo_tree_build(&t, N, Lmax, F, n_cells, refine) != 0) { free(t.child); return -1; }
+    lo_dirinfo di;
+    lo_direction_info(d, F, &di);
+    const double unit = h0 / ldexp(1.0, F) / fabs(d[di.m]);
+    const double nbg = lo_bg_occupation(m->line_nu[line], t_bg);
+    const double T0 = LO_H * m->line_nu[line] / LO_KB;
+    const int64_t M = (int64_t)N << lam;
+    const double *Kt = Kp + (size_t)line * n_cells;
+    const double *St = S + (size_t)line * n_cells;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t pix = 0; pix < M * M; pix++) {
+        if (pix % pix_stride) continue;
+        lo_odir D;
+        memset(&D, 0, sizeof(D));
+        lo_walk_octree_line(&t, &di, lam, pix / M, pix % M, &D);
+        double *I = (double *)malloc(sizeof(double) * n_ch);
+        double *phi = (double *)malloc(sizeof(double) * n_ch);
+        for (int k = 0; k < n_ch; k++) I[k] = nbg;
+        for (int64_t q = 0; q < D.n_segs; q++) {
+            const int64_t c = D.segs[q].cell;
+            const double sig = lo_sigma(sigma_turb[c], t_kin[c], m->mass_amu);
+            const double vlos = vx[c] * d[0] + vy[c] * d[1] + vz[c] * d[2];
+            lo_profile(n_ch, v_min, dv, vlos, sig, phi);
+            lo_step(1, n_ch, 1, 0, phi, (double)D.segs[q].dz * unit, 0.0, Kt + c, St + c, I,
+                    NULL, NULL, NULL);
+        }
+        for (int k = 0; k < n_ch; k++) T[pix * n_ch + k] = T0 * (I[k] - nbg);
+        free(I); free(phi); free(D.segs);
+    }
+    free(t.child);
+    return 0;
+}
+
 int lo_num_threads(void)
 {
 #ifdef _OPENMP
