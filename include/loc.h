@@ -257,6 +257,22 @@ loc_status loc_get_tex(const loc_model *m, int t, double *out, size_t n_out);
 loc_status loc_spectra(const loc_model *m, int t, const double *p_cm, int n_p,
                        double *T_out, size_t n_out);
 
+/* Emergent map of a 3D model (the final line-of-sight integration of
+ * Sect. 2, for grids and octrees) seen along direction `dir` of the model's
+ * direction table, with the current populations.  One pixel per lattice
+ * line (i, j) of level `level` of that direction (0 for grids, 0 ..
+ * octree_levels for octrees): M = n_root << level pixels per side, i along
+ * the direction's first transverse axis a, j along the second b (the two
+ * axes other than the main axis m = argmax |d|, a < b), both counted in the
+ * direction of travel (mirrored where the direction component is negative).
+ * Each pixel's ray starts with the background at the upstream face, crosses
+ * the periodic model once along the main axis through every cell it meets
+ * (every octree leaf, whatever its level) and is updated with Eq. 3, no
+ * accumulation.  T_out[(i M + j) n_ch + k] is the Rayleigh-Jeans
+ * brightness (h nu / k)(n_k - n_bg) of line t in channel k.  At most 2^26
+ * pixels per call; n_out >= M^2 n_ch, else LOC_EINVAL. */
+loc_status loc_map3d(const loc_model *m, int t, int dir, int level, double *T_out, size_t n_out);
+
 /* Number of cells (shells, grid cells or octree leaves+parents as given). */
 loc_status loc_model_info(const loc_model *m, int64_t *n_cells, int *n_levels,
                           int *n_lines, int64_t *segments_per_sim);

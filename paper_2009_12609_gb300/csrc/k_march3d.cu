@@ -97,4 +97,58 @@ loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st)
     return launch_march3d(m, a, st);
 }
 
+// ----------------------------------------------------------------------------
+// 3D map of a regular grid (Sect. 2: final line-of-sight integration): one
+// warp per pixel = root line (i, j) of direction dir, walked by the march's
+// integer DDA once through the periodic model, all channels (CMAX chunks of
+// 31 in registers), no accumulation.
+// ----------------------------------------------------------------------------
+template <int CMAX>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) map_grid3d_kernel(DevModel m, int t, int dir, float *Tout)
+{
+    const int lane = threadIdx.x & 31;
+    const long long pix = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (pix >= (long long)m.N * m.N) return;
+    const Dir3D D = m.dirs[dir];
+    GridWalk wk;
+    wk.init(D, pix / m.N, pix % m.N);
+    const int nchunk = (m.n_ch + 30) / 31;
+    const float nb = m.nbg[t];
+    const float inv_dv = (float)(1.0 / m.dv), dv = (float)m.dv, vmin = (float)m.v_min;
+    float dI[CMAX];
+#pragma unroll
+    for (int c = 0; c < CMAX; c++) dI[c] = 0.f;
+    while (true) {
+        long long cell, dz;
+        wk.step(D, m.N, cell, dz);
+        const float4 cv = m.vel[cell];
+        const float vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
+        const float2 ks = m.ks[cell * m.T + t];
+        los_step<CMAX>(dI, nchunk, lane, ks.x * ((float)dz * D.unit), ks.y - nb, (vmin + vlos) * inv_dv,
+                       dv * cv.w);
+        if (wk.done(m.N)) break;
+    }
+    los_store<CMAX>(dI, nchunk, m.n_ch, lane, (float)(kH * m.line_nu[t] / kKB), pix, Tout);
+}
+
+template <int CMAX>
+static loc_status launch_map_grid_c(const DevModel &m, int t, int dir, float *T_dev, cudaStream_t st)
+{
+    const long long np = (long long)m.N * m.N;
+    map_grid3d_kernel<CMAX><<<(unsigned)((np + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * 32, 0, st>>>(
+        m, t, dir, T_dev);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_map_grid3d(const DevModel &m, int t, int dir, float *T_dev, cudaStream_t st)
+{
+    const int nchunk = (m.n_ch + 30) / 31;
+    if (nchunk <= 2) return launch_map_grid_c<2>(m, t, dir, T_dev, st);
+    if (nchunk <= 5) return launch_map_grid_c<5>(m, t, dir, T_dev, st);
+    if (nchunk <= 9) return launch_map_grid_c<9>(m, t, dir, T_dev, st);
+    if (nchunk <= 17) return launch_map_grid_c<17>(m, t, dir, T_dev, st);
+    return launch_map_grid_c<34>(m, t, dir, T_dev, st);
+}
+
 }  // namespace loc

@@ -450,6 +450,89 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
     }
 }
 
+// ----------------------------------------------------------------------------
+// 3D map of an octree: one warp per pixel = lattice line (lam, i, j) of
+// direction dir, walked once through the periodic model across every leaf it
+// meets (a line of sight: the activation rules of the ray simulation do not
+// apply), with the step boundaries of the march and the cached descent; all
+// channels in registers, no accumulation.
+// ----------------------------------------------------------------------------
+template <int CMAX>
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) map_octree_kernel(DevModel m, int t, int dir, int lam,
+                                                                             float *Tout)
+{
+    __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const long long Mp = (long long)m.N << lam;
+    const long long pix = (long long)blockIdx.x * kOctWarpsPerBlock + wid;
+    if (pix >= Mp * Mp) return;
+    const long long H0 = 1ll << kFixedBits;
+    OctGeo g;
+    g.D = m.dirs[dir];
+    g.N = m.N;
+    g.Lmax = m.Lmax;
+    g.E = (long long)m.N << kFixedBits;
+    g.o = (H0 >> m.Lmax) / 2;
+    const long long A0 = g.o + (pix / Mp) * (H0 >> lam), B0 = g.o + (pix % Mp) * (H0 >> lam);
+    OctPathCache pc;
+    pc.p[0] = pc.p[1] = pc.p[2] = 0;
+    pc.L = -1;
+    const int nchunk = (m.n_ch + 30) / 31;
+    const float nb = m.nbg[t];
+    const float inv_dv = (float)(1.0 / m.dv), dv = (float)m.dv, vmin = (float)m.v_min;
+    float dI[CMAX];
+#pragma unroll
+    for (int c = 0; c < CMAX; c++) dI[c] = 0.f;
+    long long z = 0;
+    while (z < g.E) {
+        const long long Au = A0 + fq(g.D.qa, z), Bu = B0 + fq(g.D.qb, z);
+        long long p[3];
+        oct_point(g, Au, Bu, z, p);
+        int Lc;
+        const int cell = oct_locate_cached(m, g, p, Lc, pc, paths[wid], lane);
+        const long long HL = H0 >> Lc;
+        long long zn = oct_mlo(g, g.D.m, p[g.D.m], Lc) + HL;
+        if (g.D.qa > 0) {
+            const long long T = Au - (Au % g.E) + oct_mlo(g, g.D.a, p[g.D.a], Lc) + HL;
+            zn = min(zn, cross_z(T - A0, g.D.qa, g.D.ma));
+        }
+        if (g.D.qb > 0) {
+            const long long T = Bu - (Bu % g.E) + oct_mlo(g, g.D.b, p[g.D.b], Lc) + HL;
+            zn = min(zn, cross_z(T - B0, g.D.qb, g.D.mb));
+        }
+        zn = min(zn, g.E);
+        const int leaf = __ldg(m.leaf_of + cell);
+        const float4 cv = m.vel[leaf];
+        const float vlos = cv.x * g.D.d[0] + cv.y * g.D.d[1] + cv.z * g.D.d[2];
+        const float2 ks = m.ks[(long long)leaf * m.T + t];
+        los_step<CMAX>(dI, nchunk, lane, ks.x * ((float)(zn - z) * g.D.unit), ks.y - nb,
+                       (vmin + vlos) * inv_dv, dv * cv.w);
+        z = zn;
+    }
+    los_store<CMAX>(dI, nchunk, m.n_ch, lane, (float)(kH * m.line_nu[t] / kKB), pix, Tout);
+}
+
+template <int CMAX>
+static loc_status launch_map_oct_c(const DevModel &m, int t, int dir, int lam, float *T_dev, cudaStream_t st)
+{
+    const long long Mp = (long long)m.N << lam;
+    const long long nb = (Mp * Mp + kOctWarpsPerBlock - 1) / kOctWarpsPerBlock;
+    map_octree_kernel<CMAX><<<(unsigned)nb, kOctWarpsPerBlock * 32, 0, st>>>(m, t, dir, lam, T_dev);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_map_octree(const DevModel &m, int t, int dir, int lam, float *T_dev, cudaStream_t st)
+{
+    const int nchunk = (m.n_ch + 30) / 31;
+    if (nchunk <= 2) return launch_map_oct_c<2>(m, t, dir, lam, T_dev, st);
+    if (nchunk <= 5) return launch_map_oct_c<5>(m, t, dir, lam, T_dev, st);
+    if (nchunk <= 9) return launch_map_oct_c<9>(m, t, dir, lam, T_dev, st);
+    if (nchunk <= 17) return launch_map_oct_c<17>(m, t, dir, lam, T_dev, st);
+    return launch_map_oct_c<34>(m, t, dir, lam, T_dev, st);
+}
+
 int octree_persistent_warps(const DevModel &m)
 {
     (void)m;

@@ -62,17 +62,32 @@ loc_status launch_bg(const DevModel &m, cudaStream_t st)
     return LOC_OK;
 }
 
-__global__ void line_params_kernel(DevModel m)
+// zero_acc: 0 keep the accumulators; 1 (2) also clear the FP32 (FP64)
+// accumulators of entry idx, NORM of its cell and the convergence metric,
+// the start of a ray simulation in the ALI loop
+__global__ void line_params_kernel(DevModel m, int zero_acc)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)m.T * m.n_cells) return;
     line_params_one(m, idx);
+    if (zero_acc) {
+        const bool first = (idx % m.T) == 0;
+        if (zero_acc == 2) {
+            m.acc64[2 * idx] = 0.0;
+            m.acc64[2 * idx + 1] = 0.0;
+            if (first) m.norm64[idx / m.T] = 0.0;
+        } else {
+            m.acc[idx] = make_float2(0.f, 0.f);
+            if (first) m.norm[idx / m.T] = 0.f;
+        }
+        if (idx == 0) *m.dtex_bits = 0u;
+    }
 }
 
-loc_status launch_line_params(const DevModel &m, cudaStream_t st)
+loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc)
 {
     const long long n = (long long)m.T * m.n_cells;
-    line_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m);
+    line_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, zero_acc);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

@@ -552,11 +552,13 @@ static loc_status ensure_runs(loc_model *m, int len)
 // one ray simulation: zero the accumulators, then the march over all
 // (ray, line group) work items -- one launch, or for 1D rays cut into runs
 // the affine / scan / run launches
-static loc_status march_impl(loc_model *m, const loc_iter_opts *o)
+static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed = false)
 {
     DevModel &D = m->d;
     const int fp64 = o->precision == LOC_FP64_ACC;
-    if (fp64) {
+    if (zeroed) {
+        // the line-parameter launch of this iteration cleared the accumulators
+    } else if (fp64) {
         LOC_CUDA_TRY(cudaMemsetAsync(D.acc64, 0, sizeof(double) * 2 * D.T * D.n_cells, m->st));
         LOC_CUDA_TRY(cudaMemsetAsync(D.norm64, 0, sizeof(double) * D.n_cells, m->st));
     } else {
@@ -710,10 +712,9 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     for (it = 0; it < o->max_iter; it++) {
         const size_t b = 4 * (size_t)it;
         if (mark(b) != cudaSuccess) { st = LOC_ECUDA; break; }
-        if ((st = launch_line_params(D, m->st)) != LOC_OK) break;
+        if ((st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1)) != LOC_OK) break;
         if (mark(b + 1) != cudaSuccess) { st = LOC_ECUDA; break; }
-        if ((st = march_impl(m, o)) != LOC_OK) break;
-        if (cudaMemsetAsync(D.dtex_bits, 0, sizeof(unsigned), m->st) != cudaSuccess) { st = LOC_ECUDA; break; }
+        if ((st = march_impl(m, o, true)) != LOC_OK) break;
         if (mark(b + 2) != cudaSuccess) { st = LOC_ECUDA; break; }
         if ((st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st)) != LOC_OK) break;
         if (mark(b + 3) != cudaSuccess) { st = LOC_ECUDA; break; }
@@ -881,6 +882,41 @@ loc_status loc_spectra(const loc_model *m, int t, const double *p_cm, int n_p, d
         }
     }
     if (e != cudaSuccess) { set_error("spectra failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    if (s == LOC_OK) for (size_t i = 0; i < n; i++) T_out[i] = tmp[i];
+    cudaStreamSynchronize(m->st);
+    dev_free_all(mm, tmp_mem);
+    return s;
+}
+
+loc_status loc_map3d(const loc_model *m, int t, int dir, int level, double *T_out, size_t n_out)
+{
+    if (!m || !T_out) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
+    const DevModel &D = m->d;
+    if (D.geometry != LOC_GRID_3D && D.geometry != LOC_OCTREE_3D) { set_error("loc_map3d needs a 3D model"); return LOC_EINVAL; }
+    if (t < 0 || t >= D.T) { set_error("line index %d out of range", t); return LOC_EINVAL; }
+    if (dir < 0 || dir >= D.n_dir) { set_error("direction index %d out of range [0, %d)", dir, D.n_dir); return LOC_EINVAL; }
+    const int lmax = (D.geometry == LOC_OCTREE_3D) ? D.Lmax : 0;
+    if (level < 0 || level > lmax) { set_error("map level must be in [0, %d]", lmax); return LOC_EINVAL; }
+    const long long Mp = (long long)D.N << level;
+    if (Mp * Mp > (1ll << 26)) { set_error("map of %lld^2 pixels exceeds 2^26 pixels", Mp); return LOC_EINVAL; }
+    const size_t n = (size_t)(Mp * Mp) * D.n_ch;
+    if (n_out < n) { set_error("output needs %zu elements", n); return LOC_EINVAL; }
+    loc_model *mm = const_cast<loc_model *>(m);
+    std::vector<void *> tmp_mem;
+    float *Td = (float *)dev_alloc(mm, sizeof(float) * n, tmp_mem);
+    if (!Td) { set_error("allocation of the map buffer failed"); return LOC_ENOMEM; }
+    std::vector<float> tmp;
+    try { tmp.resize(n); } catch (...) { dev_free_all(mm, tmp_mem); set_error("host allocation failed"); return LOC_ENOMEM; }
+    loc_status s = launch_line_params(D, m->st);
+    if (s == LOC_OK) s = (D.geometry == LOC_GRID_3D) ? launch_map_grid3d(D, t, dir, Td, m->st)
+                                                     : launch_map_octree(D, t, dir, level, Td, m->st);
+    cudaError_t e = cudaSuccess;
+    if (s == LOC_OK) {
+        e = cudaMemcpyAsync(tmp.data(), Td, sizeof(float) * n, cudaMemcpyDeviceToHost, m->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+        if (e != cudaSuccess) { set_error("map failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    }
     if (s == LOC_OK) for (size_t i = 0; i < n; i++) T_out[i] = tmp[i];
     cudaStreamSynchronize(m->st);
     dev_free_all(mm, tmp_mem);

@@ -158,7 +158,7 @@ inline bool distinct_level_pairs(const int32_t *u, const int32_t *l, int n, int 
 // kernel launchers (one per translation unit)
 loc_status launch_geom1d(const DevModel &m, cudaStream_t st);
 loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W);
-loc_status launch_line_params(const DevModel &m, cudaStream_t st);
+loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc = 0);
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st);
@@ -183,6 +183,8 @@ loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long 
                                unsigned long long *count, cudaStream_t st,
                                unsigned long long *sums = nullptr, unsigned *fam_work = nullptr);
 int octree_persistent_warps(const DevModel &m);
+loc_status launch_map_grid3d(const DevModel &m, int t, int dir, float *T_dev, cudaStream_t st);
+loc_status launch_map_octree(const DevModel &m, int t, int dir, int lam, float *T_dev, cudaStream_t st);
 constexpr int kOctMaxKids = 96;         // child lines one frame can hold
 loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,
                              double *norm, cudaStream_t st);

@@ -118,7 +118,7 @@ EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecul
            "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
            "loc_radiation1d_noalloc", "loc_autotune", "loc_server_create",
            "loc_server_submit", "loc_server_poll", "loc_server_stats", "loc_server_destroy",
-           "loc_trace_octree", "loc_octree_path_sums"]
+           "loc_trace_octree", "loc_octree_path_sums", "loc_map3d"]
 
 
 def library_path():
@@ -149,6 +149,7 @@ def load():
     lib.loc_set_populations.argtypes = [_vp, _d, ctypes.c_size_t]
     lib.loc_get_tex.argtypes = [_vp, ctypes.c_int, _d, ctypes.c_size_t]
     lib.loc_spectra.argtypes = [_vp, ctypes.c_int, _d, ctypes.c_int, _d, ctypes.c_size_t]
+    lib.loc_map3d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, ctypes.c_size_t]
     lib.loc_model_info.argtypes = [_vp, _i64, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), _i64]
     lib.loc_trace_ray.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
@@ -408,6 +409,13 @@ def loc_spectra(h, t, p_cm, n_ch):
     return out
 
 
+def loc_map3d(h, t, d, level, n_pix_side, n_ch):
+    """T_RJ [M * M][n_ch] map of line t along direction d, M = n_pix_side."""
+    out = np.zeros((int(n_pix_side) ** 2, int(n_ch)))
+    _check(load().loc_map3d(h, int(t), int(d), int(level), _pd(out), out.size))
+    return out
+
+
 def loc_trace_ray(h, d, i, j, cap=1 << 16):
     cells = np.zeros(cap, np.int64)
     dz = np.zeros(cap, np.int64)
@@ -486,6 +494,12 @@ class Model:
 
     def spectra(self, t, p_cm):
         return loc_spectra(self.h, t, p_cm, self.model["n_ch"])
+
+    def map3d(self, t, d, level=0):
+        """Emergent map of line t along direction d of the model's table:
+        T_RJ [M * M][n_ch], M = n_root << level, pixel (i, j) at i * M + j."""
+        return loc_map3d(self.h, t, d, level, int(self.model["n_root"]) << int(level),
+                         self.model["n_ch"])
 
     def info(self):
         return loc_model_info(self.h)
