@@ -400,19 +400,22 @@ __device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchA
 // I <- I + (S - I)(1 - e^-tau) gives A <- A - A t, B <- B + (S - B) t,
 // t = 1 - e^-tau.  The channel window, profile and t are evaluated exactly
 // as in march_step, so the run's map reproduces the sequential march up to
-// rounding.
+// rounding.  Only channels [tlo, thi) are updated; A and B hold them at
+// A[t * tile + k - tlo].
 template <int G>
 __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &a, float *A, float *B,
-                                            const Step<G> &st, int lane)
+                                            const Step<G> &st, int lane, int tlo, int thi)
 {
-    const int nch = m.n_ch;
     float u0, db;
     int klo, khi;
     step_window(m, a, st, u0, db, klo, khi);
+    klo = max(klo, tlo);
+    khi = min(khi, thi);
     float Ks[G];
 #pragma unroll
     for (int t = 0; t < G; t++) Ks[t] = step_ks(st.ks[t].x, st.s);
     const bool full = (a.n_lines == G);
+    const int tile = a.tile;
     for (int base = klo; base < khi; base += 31) {
         const int k = base + lane;
         const float b0 = ((float)k + u0) * db;
@@ -425,7 +428,7 @@ __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &
             for (int t = 0; t < G; t++) {
                 if (full || t < a.n_lines) {
                     const float tm = one_minus_exp(Ks[t] * phi);
-                    const int o = t * nch + k;
+                    const int o = t * tile + k - tlo;
                     const float av = A[o], bv = B[o];
                     A[o] = fmaf(-av, tm, av);
                     B[o] = fmaf(st.ks[t].y - bv, tm, bv);

@@ -66,6 +66,33 @@ loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st
 //   march:   per (run, line group) march_step over the run from its I_in,
 //            accumulating SIJ / ESC / NORM exactly as the whole-ray march.
 // ----------------------------------------------------------------------------
+// Channels [lo, hi) touched by the windows of steps s0 .. s0 + n - 1 (the
+// union of step_window over the run; lo = hi = 0 if none): all lanes.
+template <int G>
+__device__ __forceinline__ int2 run_window_union(const DevModel &m, const MarchArgs &a, int s0, int n, int lane)
+{
+    int lo = m.n_ch, hi = 0;
+    for (int q = lane; q < n; q += 32) {
+        const Seg1D rec = m.segs[s0 + q];
+        Step<G> st;
+        st.vlos = rec.vlos;
+        st.inv = m.inv_s2sig[rec.cell];
+        float u0, db;
+        int klo, khi;
+        step_window(m, a, st, u0, db, klo, khi);
+        if (khi > klo) {
+            lo = min(lo, klo);
+            hi = max(hi, khi);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(kFull, lo, off));
+        hi = max(hi, __shfl_xor_sync(kFull, hi, off));
+    }
+    return (lo < hi) ? make_int2(lo, hi) : make_int2(0, 0);
+}
+
 template <int G>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_affine_kernel(DevModel m, MarchArgs a0)
 {
@@ -75,28 +102,47 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_affine_kernel(Dev
     const long long item = (long long)blockIdx.x * kWarpsPerBlock + wid;
     if (item >= a0.n_chunks * a0.n_groups) return;
     const long long gc = item / a0.n_groups;
-    const MarchArgs a = warp_args(m, a0, (int)(item - gc * a0.n_groups));
+    const int g = (int)(item - gc * a0.n_groups);
+    const MarchArgs a = warp_args(m, a0, g);
     const int j = a.chunk_ray[gc];
     const int c = (int)(gc - a.chunk_off[j]);
     const int n = m.ray_off[j + 1] - m.ray_off[j];
     const int q0 = c * a.chunk;
+    const int len = min(a.chunk, n - q0);
+    const int s0 = m.ray_off[j] + q0;
+    // the channels this run touches; the scan and the run launch use them too
+    const int2 rng = run_window_union<G>(m, a, s0, len, lane);
+    if (g == 0 && lane == 0) a.run_rng[gc] = rng;
     if (q0 + a.chunk >= n) return;                 // last run of the ray: map not needed
-    const int nch = m.n_ch;
-    float *A = smem + (size_t)wid * 2 * a.per * nch;
-    float *B = A + a.per * nch;
-    for (int i = lane; i < a.n_lines * nch; i += 32) {
-        A[i] = 1.f;
-        B[i] = 0.f;
+    const int nch = m.n_ch, tile = a.tile;
+    float *A = smem + (size_t)wid * 2 * a.per * tile;
+    float *B = A + a.per * tile;
+    // channel tiles of the union: each tile composes its own channels' maps
+    for (int tlo = rng.x; tlo < rng.y; tlo += tile) {
+        const int thi = min(rng.y, tlo + tile), w = thi - tlo;
+        for (int i = lane; i < G * w; i += 32) {
+            const int t = i / w;
+            A[t * tile + i - t * w] = 1.f;
+            B[t * tile + i - t * w] = 0.f;
+        }
+        __syncwarp();
+        walk_steps1d<G>(m, a, s0, a.chunk, lane, [&](const Step<G> &st) {
+            affine_step<G>(m, a, A, B, st, lane, tlo, thi);
+            return 0ll;
+        });
+        float2 *out = a.ab + ((size_t)gc * m.T + a.line0) * nch + tlo;
+        for (int i = lane; i < a.n_lines * w; i += 32) {
+            const int t = i / w, k = i - t * w;
+            out[(size_t)t * nch + k] = make_float2(A[t * tile + k], B[t * tile + k]);
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    walk_steps1d<G>(m, a, m.ray_off[j] + q0, a.chunk, lane, [&](const Step<G> &st) {
-        affine_step<G>(m, a, A, B, st, lane);
-        return 0ll;
-    });
-    float2 *out = a.ab + ((size_t)gc * m.T + a.line0) * nch;
-    for (int i = lane; i < a.n_lines * nch; i += 32) out[i] = make_float2(A[i], B[i]);
 }
 
+// thread per (ray, line, channel): the entering intensity of every run of
+// the ray, from the background through the runs' maps in ray order; a run
+// whose windows miss the channel leaves it unchanged and needs no value.
+// Maps are loaded eight runs at a time ahead of the dependent updates.
 __global__ void march1d_scan_kernel(DevModel m, MarchArgs a)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,14 +150,31 @@ __global__ void march1d_scan_kernel(DevModel m, MarchArgs a)
     if (idx >= (long long)m.n_rays * T * nch) return;
     const int j = (int)(idx / ((long long)T * nch));
     const int rem = (int)(idx - (long long)j * T * nch);      // t * nch + k
-    const int t = rem / nch;
+    const int t = rem / nch, k = rem - t * nch;
     float I = m.nbg[t];
     const int c0 = a.chunk_off[j], c1 = a.chunk_off[j + 1];
-    for (int c = c0; c < c1; c++) {
-        float2 *p = a.ab + (size_t)c * T * nch + rem;
-        const float2 v = *p;
-        p->x = I;
-        if (c + 1 < c1) I = fmaf(v.x, I, v.y);
+    constexpr int kB = 8;
+    for (int cb = c0; cb < c1; cb += kB) {
+        float2 v[kB];
+        bool in[kB];
+#pragma unroll
+        for (int q = 0; q < kB; q++) {
+            const int c = cb + q;
+            in[q] = false;
+            if (c < c1) {
+                const int2 r = a.run_rng[c];
+                in[q] = (k >= r.x && k < r.y);
+                if (in[q] && c + 1 < c1) v[q] = a.ab[(size_t)c * T * nch + rem];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kB; q++) {
+            const int c = cb + q;
+            if (c < c1 && in[q]) {
+                a.ab[(size_t)c * T * nch + rem].x = I;
+                if (c + 1 < c1) I = fmaf(v[q].x, I, v[q].y);
+            }
+        }
     }
 }
 
@@ -132,8 +195,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_run_kernel(DevMod
     const int len = min(a.chunk, n - q0);
     const int nch = m.n_ch;
     float *I = smem + (size_t)wid * a.per * nch;
-    const float2 *in = a.ab + ((size_t)gc * m.T + a.line0) * nch;
-    for (int i = lane; i < a.n_lines * nch; i += 32) I[i] = in[i].x;
+    // entering intensities of the channels the run's windows touch (the
+    // march reads no other channel)
+    const int2 rng = a.run_rng[gc];
+    const int w = rng.y - rng.x;
+    const float2 *in = a.ab + ((size_t)gc * m.T + a.line0) * nch + rng.x;
+    for (int i = lane; i < a.n_lines * w; i += 32) {
+        const int t = i / w, k = i - t * w;
+        I[t * nch + rng.x + k] = in[(size_t)t * nch + k].x;
+    }
     __syncwarp();
     const long long nw = walk_steps1d<G>(m, a, m.ray_off[j] + q0, len, lane, [&](const Step<G> &st) {
         return (long long)march_step<G>(m, a, I, st, lane);
@@ -146,7 +216,7 @@ static loc_status launch_chunked_g(const DevModel &m, const MarchArgs &a, cudaSt
 {
     const long long items = a.n_chunks * a.n_groups;
     const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const size_t smem_a = (size_t)kWarpsPerBlock * 2 * a.per * m.n_ch * sizeof(float);
+    const size_t smem_a = (size_t)kWarpsPerBlock * 2 * a.per * a.tile * sizeof(float);
     const size_t smem_r = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
     LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_affine_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
     LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_run_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));

@@ -50,6 +50,7 @@ struct loc_model {
     int run_len = 0;                 // 1D: run length of the current run tables (0: none)
     long long run_n = 0;             // runs in the current tables
     int *run_off = nullptr, *run_ray = nullptr;
+    int2 *run_rng = nullptr;         // channel range each run's windows touch
     float2 *run_ab = nullptr;        // run maps / entering intensities
     size_t run_ab_bytes = 0;
     std::vector<void *> run_mem, run_ab_mem;
@@ -533,6 +534,7 @@ static loc_status ensure_runs(loc_model *m, int len)
         m->run_len = 0;
         TRY(upload(m, &m->run_off, off.data(), off.size(), m->run_mem, "run offsets"));
         TRY(upload(m, &m->run_ray, ray.data(), ray.size(), m->run_mem, "run rays"));
+        TRY(upload<int2>(m, &m->run_rng, nullptr, ray.size(), m->run_mem, "run ranges"));
         LOC_CUDA_TRY(cudaStreamSynchronize(m->st));   // host tables leave scope
         m->run_len = len;
         m->run_n = off[D.n_rays];
@@ -569,8 +571,9 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
     memset(&a, 0, sizeof(a));
     a.per = lines_per_warp(m, o);
     const int run = steps_per_run(m, o, a.per);
-    // the affine launch keeps two [per][n_ch] arrays per warp in shared memory
-    if (run > 0) while (a.per > 1 && 32ll * a.per * D.n_ch > 200 * 1024) a.per--;
+    // the affine launch keeps two [per][tile] arrays per warp in shared memory
+    const int tile = std::min(D.n_ch, kRunTile);
+    if (run > 0) while (a.per > 1 && 32ll * a.per * tile > 200 * 1024) a.per--;
     if (D.geometry == LOC_OCTREE_3D) {
         const size_t need = (size_t)octree_persistent_warps(D) * 10 * a.per * D.n_ch;
         if (need > m->oct_scratch_floats) {
@@ -593,6 +596,8 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
         a.chunk_off = m->run_off;
         a.chunk_ray = m->run_ray;
         a.ab = m->run_ab;
+        a.run_rng = m->run_rng;
+        a.tile = tile;
         if (a.n_chunks > 0) TRY(launch_march1d_chunked(D, a, m->st));
     } else {
         TRY(launch_march(D, a, m->st));

@@ -23,6 +23,7 @@ constexpr int kMaxLevels = 32;      // molecule levels supported by the SE
 constexpr int kMaxLines = 64;       // radiative lines
 constexpr int kMaxChannels = 1024;
 constexpr int kMaxLinesPerWarp = 15;
+constexpr int kRunTile = 128;       // channels per shared-memory tile of a 1D run map
 
 // One step of a 1D ray through one shell, precomputed at model creation:
 // cell index, path length s (cm), line-of-sight velocity at the step's
@@ -125,6 +126,8 @@ struct MarchArgs {
     const int *chunk_off;   // [n_rays + 1] first run of each ray
     const int *chunk_ray;   // [n_chunks] ray of each run
     float2 *ab;             // [n_chunks][T][n_ch] run maps {alpha, beta}, then {I_in, -}
+    int2 *run_rng;          // [n_chunks] channels [lo, hi) the run's step windows touch
+    int tile;               // channels per shared-memory tile of the run maps
 };
 
 // ----------------------------------------------------------------------------
