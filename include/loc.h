@@ -223,7 +223,7 @@ loc_status loc_march(loc_model *m, const loc_iter_opts *o);
 /* Choose the launch shape of the march: the number of lines each warp
  * carries (more lines per warp share the profile and the walk, fewer give
  * more warps and fewer registers per thread) and, for 1D models, the run
- * length steps_per_chunk (whole rays or runs of 128 / 64 / 32 / 16 steps),
+ * length steps_per_chunk (whole rays or runs of 128 / 64 / 32 / 16 / 8 steps),
  * by timing one ray simulation per candidate with CUDA events on the
  * model's stream; the fastest is used by later calls whose lines_per_pass
  * (steps_per_chunk) is 0.  Runs ray simulations with the current

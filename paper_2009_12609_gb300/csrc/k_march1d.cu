@@ -93,6 +93,32 @@ __device__ __forceinline__ int2 run_window_union(const DevModel &m, const MarchA
     return (lo < hi) ? make_int2(lo, hi) : make_int2(0, 0);
 }
 
+// warp per run: the run's window union, and the widest union of all runs
+// (sizes the affine launch's shared-memory tiles)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_ranges_kernel(DevModel m, MarchArgs a, int *max_w)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gc = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (gc >= a.n_chunks) return;
+    const int j = a.chunk_ray[gc];
+    const int c = (int)(gc - a.chunk_off[j]);
+    const int n = m.ray_off[j + 1] - m.ray_off[j];
+    const int q0 = c * a.chunk;
+    const int2 rng = run_window_union<1>(m, a, m.ray_off[j] + q0, min(a.chunk, n - q0), lane);
+    if (lane == 0) {
+        a.run_rng[gc] = rng;
+        atomicMax(max_w, rng.y - rng.x);
+    }
+}
+
+loc_status launch_march1d_ranges(const DevModel &m, const MarchArgs &a, int *max_w_dev, cudaStream_t st)
+{
+    const long long nb = (a.n_chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    march1d_ranges_kernel<<<(unsigned)nb, kWarpsPerBlock * 32, 0, st>>>(m, a, max_w_dev);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_affine_kernel(DevModel m, MarchArgs a0)
 {
@@ -102,18 +128,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_affine_kernel(Dev
     const long long item = (long long)blockIdx.x * kWarpsPerBlock + wid;
     if (item >= a0.n_chunks * a0.n_groups) return;
     const long long gc = item / a0.n_groups;
-    const int g = (int)(item - gc * a0.n_groups);
-    const MarchArgs a = warp_args(m, a0, g);
+    const MarchArgs a = warp_args(m, a0, (int)(item - gc * a0.n_groups));
     const int j = a.chunk_ray[gc];
     const int c = (int)(gc - a.chunk_off[j]);
     const int n = m.ray_off[j + 1] - m.ray_off[j];
     const int q0 = c * a.chunk;
-    const int len = min(a.chunk, n - q0);
     const int s0 = m.ray_off[j] + q0;
-    // the channels this run touches; the scan and the run launch use them too
-    const int2 rng = run_window_union<G>(m, a, s0, len, lane);
-    if (g == 0 && lane == 0) a.run_rng[gc] = rng;
     if (q0 + a.chunk >= n) return;                 // last run of the ray: map not needed
+    const int2 rng = a.run_rng[gc];                // the channels this run touches
     const int nch = m.n_ch, tile = a.tile;
     float *A = smem + (size_t)wid * 2 * a.per * tile;
     float *B = A + a.per * tile;

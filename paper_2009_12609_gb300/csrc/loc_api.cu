@@ -51,6 +51,10 @@ struct loc_model {
     long long run_n = 0;             // runs in the current tables
     int *run_off = nullptr, *run_ray = nullptr;
     int2 *run_rng = nullptr;         // channel range each run's windows touch
+    int *run_maxw = nullptr;         // device scalar: widest range
+    int rng_len = 0;                 // run length and window of the current ranges
+    double rng_window = -1.0;
+    int run_tile = 0;                // widest range, rounded up to 32 channels
     float2 *run_ab = nullptr;        // run maps / entering intensities
     size_t run_ab_bytes = 0;
     std::vector<void *> run_mem, run_ab_mem;
@@ -421,6 +425,7 @@ loc_status loc_set_molecule(loc_model *m, const loc_molecule_desc *mol)
     dev_free_all(m, m->mol_mem);
     m->has_mol = false;
     m->has_rad = false;
+    m->rng_len = 0;                  // line widths change with the molecule
     loc_status s = set_molecule_impl(m, mol);
     if (s != LOC_OK) {
         cudaStreamSynchronize(m->st);
@@ -535,9 +540,11 @@ static loc_status ensure_runs(loc_model *m, int len)
         TRY(upload(m, &m->run_off, off.data(), off.size(), m->run_mem, "run offsets"));
         TRY(upload(m, &m->run_ray, ray.data(), ray.size(), m->run_mem, "run rays"));
         TRY(upload<int2>(m, &m->run_rng, nullptr, ray.size(), m->run_mem, "run ranges"));
+        TRY(upload<int>(m, &m->run_maxw, nullptr, 1, m->run_mem, "run range width"));
         LOC_CUDA_TRY(cudaStreamSynchronize(m->st));   // host tables leave scope
         m->run_len = len;
         m->run_n = off[D.n_rays];
+        m->rng_len = 0;
     }
     const size_t need = sizeof(float2) * (size_t)std::max(m->run_n, 1ll) * D.T * D.n_ch;
     if (need > m->run_ab_bytes) {
@@ -571,9 +578,34 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
     memset(&a, 0, sizeof(a));
     a.per = lines_per_warp(m, o);
     const int run = steps_per_run(m, o, a.per);
-    // the affine launch keeps two [per][tile] arrays per warp in shared memory
-    const int tile = std::min(D.n_ch, kRunTile);
-    if (run > 0) while (a.per > 1 && 32ll * a.per * tile > 200 * 1024) a.per--;
+    a.window = (float)o->window_sigmas;
+    a.inv_dv = (float)(1.0 / D.dv);
+    if (run > 0) {
+        TRY(ensure_runs(m, run));
+        a.chunk = run;
+        a.n_chunks = m->run_n;
+        a.chunk_off = m->run_off;
+        a.chunk_ray = m->run_ray;
+        a.ab = m->run_ab;
+        a.run_rng = m->run_rng;
+        // each run's window union depends only on the model, the run length
+        // and the window: found once, it sizes the affine launch's tiles
+        if (m->rng_len != run || m->rng_window != o->window_sigmas) {
+            int w = 0;
+            if (a.n_chunks > 0) {
+                LOC_CUDA_TRY(cudaMemsetAsync(m->run_maxw, 0, sizeof(int), m->st));
+                TRY(launch_march1d_ranges(D, a, m->run_maxw, m->st));
+                LOC_CUDA_TRY(cudaMemcpyAsync(&w, m->run_maxw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+                LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+            }
+            m->run_tile = std::min(D.n_ch, std::max(32, (w + 31) / 32 * 32));
+            m->rng_len = run;
+            m->rng_window = o->window_sigmas;
+        }
+        a.tile = m->run_tile;
+        // the affine launch keeps two [per][tile] arrays per warp in shared memory
+        while (a.per > 1 && 32ll * a.per * a.tile > 200 * 1024) a.per--;
+    }
     if (D.geometry == LOC_OCTREE_3D) {
         const size_t need = (size_t)octree_persistent_warps(D) * 10 * a.per * D.n_ch;
         if (need > m->oct_scratch_floats) {
@@ -585,19 +617,9 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
         }
     }
     a.n_groups = (D.T + a.per - 1) / a.per;
-    a.window = (float)o->window_sigmas;
-    a.inv_dv = (float)(1.0 / D.dv);
     a.fp64_acc = fp64;
     a.count = o->profile;
     if (run > 0) {
-        TRY(ensure_runs(m, run));
-        a.chunk = run;
-        a.n_chunks = m->run_n;
-        a.chunk_off = m->run_off;
-        a.chunk_ray = m->run_ray;
-        a.ab = m->run_ab;
-        a.run_rng = m->run_rng;
-        a.tile = tile;
         if (a.n_chunks > 0) TRY(launch_march1d_chunked(D, a, m->st));
     } else {
         TRY(launch_march(D, a, m->st));
@@ -632,7 +654,7 @@ loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int
     if (D.geometry == LOC_SHELLS_1D) {
         int longest = 0;
         for (int j = 0; j < D.n_rays; j++) longest = std::max(longest, m->ray_off_h[j + 1] - m->ray_off_h[j]);
-        for (int len : {128, 64, 32, 16})
+        for (int len : {128, 64, 32, 16, 8})
             if (len < longest) runs.push_back(len);
     }
     TRY(launch_line_params(m->d, m->st));

@@ -23,7 +23,6 @@ constexpr int kMaxLevels = 32;      // molecule levels supported by the SE
 constexpr int kMaxLines = 64;       // radiative lines
 constexpr int kMaxChannels = 1024;
 constexpr int kMaxLinesPerWarp = 15;
-constexpr int kRunTile = 128;       // channels per shared-memory tile of a 1D run map
 
 // One step of a 1D ray through one shell, precomputed at model creation:
 // cell index, path length s (cm), line-of-sight velocity at the step's
@@ -127,7 +126,7 @@ struct MarchArgs {
     const int *chunk_ray;   // [n_chunks] ray of each run
     float2 *ab;             // [n_chunks][T][n_ch] run maps {alpha, beta}, then {I_in, -}
     int2 *run_rng;          // [n_chunks] channels [lo, hi) the run's step windows touch
-    int tile;               // channels per shared-memory tile of the run maps
+    int tile;               // channels per shared-memory tile of the run maps (>= every run's union)
 };
 
 // ----------------------------------------------------------------------------
@@ -165,6 +164,7 @@ loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc =
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st);
+loc_status launch_march1d_ranges(const DevModel &m, const MarchArgs &a, int *max_w_dev, cudaStream_t st);
 loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);
 loc_status launch_lte(const DevModel &m, cudaStream_t st);
