@@ -141,15 +141,22 @@ def line_params(mol, model, x, n_levels=None):
     return Kp, S
 
 
+def _ray_power(model):
+    """Exponent a of the impact parameters p_j = R ((j + 1/2) / n)^a (1: equidistant)."""
+    a = float(model.get("ray_power", 0.0) or 0.0)
+    return ctypes.c_double(a if a > 0.0 else 1.0)
+
+
 def paths_1d(model, j):
-    """Segment list (cell, s, cos) of equidistant ray j of a 1D model."""
+    """Segment list (cell, s, cos) of ray j of a 1D model."""
     lib = _load()
     R = _f64(model["radius"])
     K = len(R)
     cell = np.zeros(2 * K + 2, np.int32)
     s = np.zeros(2 * K + 2)
     cv = np.zeros(2 * K + 2)
-    n = lib.lo_paths_1d(K, _p(R), int(model["n_rays"]), int(j), _p(cell), _p(s), _p(cv))
+    n = lib.lo_paths_1d(K, _p(R), int(model["n_rays"]), _ray_power(model), int(j), _p(cell), _p(s),
+                        _p(cv))
     return cell[:n].copy(), s[:n].copy(), cv[:n].copy()
 
 
@@ -157,7 +164,7 @@ def weights_1d(model):
     lib = _load()
     R = _f64(model["radius"])
     W = np.zeros(len(R))
-    lib.lo_weights_1d(len(R), _p(R), int(model["n_rays"]), _p(W))
+    lib.lo_weights_1d(len(R), _p(R), int(model["n_rays"]), _ray_power(model), _p(W))
     return W
 
 
@@ -172,7 +179,7 @@ def march_1d(mol, model, Kp, S, n_levels=None):
     lib.lo_march_1d(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["t_kin"])),
                     _p(_f64(model["sigma_turb"])), _p(_f64(model["v"])),
                     int(model["n_ch"]), ctypes.c_double(model["v_min"]),
-                    ctypes.c_double(model["dv"]), int(model["n_rays"]),
+                    ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
                     ctypes.c_double(model["t_bg"]), _p(_f64(Kp)), _p(_f64(S)),
                     _p(SIJ), _p(ESC), _p(NORM))
     return SIJ, ESC, NORM
@@ -219,7 +226,7 @@ def iterate_1d(mol, model, n_iter, ali=True, x0=None, n_levels=None):
                             _p(_f64(model["t_kin"])), _p(_f64(model["sigma_turb"])),
                             _p(_f64(model["abundance"])), _p(_f64(model["v"])),
                             int(model["n_ch"]), ctypes.c_double(model["v_min"]),
-                            ctypes.c_double(model["dv"]), int(model["n_rays"]),
+                            ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
                             ctypes.c_double(model["t_bg"]), int(bool(ali)), int(n_iter),
                             _p(x), _p(dt))
     if bad:

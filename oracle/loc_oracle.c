@@ -189,9 +189,12 @@ static void lo_step(int n_lines, int n_ch, int n_cells, int cell,
 
 /* ------------------------------------------------------------------------ */
 /* 1D geometry (Sect. 2.1): concentric shells with outer radii R_k; rays are */
-/* parallel with impact parameters p; ray j of n_rays equidistant rays has   */
-/* p_j = (j + 1/2) R / n_rays and stands for the annulus of area             */
-/* A_j = pi R^2 ((j+1)^2 - j^2) / n_rays^2.  A ray with impact parameter p   */
+/* parallel with impact parameters p; ray j of n_rays stands for the annulus */
+/* between b_j = R (j / n_rays)^a and b_{j+1}, area A_j = pi (b_{j+1}^2 -   */
+/* b_j^2), and passes at p_j = R ((j + 1/2) / n_rays)^a: equidistant rays    */
+/* for a = 1 (the default), a power law otherwise (Sect. 2.1; our reading of */
+/* the power-law option, which the paper does not spell out).  A ray with   */
+/* impact parameter p                                                        */
 /* visits shells K-1 .. t+1, the tangent shell t (smallest k with R_k > p)   */
 /* in two halves, then t+1 .. K-1.  Path lengths are                         */
 /*   s = sqrt(R_k^2 - p^2) - sqrt(R_{k-1}^2 - p^2),  tangent halves          */
@@ -201,6 +204,16 @@ static void lo_step(int n_lines, int n_ch, int n_cells, int cell,
 /* point; the outbound half of the tangent shell starts at cos = 0.          */
 /* ------------------------------------------------------------------------ */
 typedef struct { int cell; double s; double cosv; } lo_seg1d;
+
+/* impact parameter and annulus area of ray j (a <= 0 means a = 1) */
+static void lo_ray_1d(double Rout, int n_rays, double a, int j, double *p, double *A)
+{
+    if (!(a > 0.0)) a = 1.0;
+    const double n = (double)n_rays;
+    const double b0 = Rout * pow(j / n, a), b1 = Rout * pow((j + 1.0) / n, a);
+    *p = Rout * pow((j + 0.5) / n, a);
+    *A = LO_PI * (b1 * b1 - b0 * b0);
+}
 
 static int lo_tangent_shell(int K, const double *R, double p)
 {
@@ -231,11 +244,12 @@ static int lo_ray_segments_1d(int K, const double *R, double p, lo_seg1d *segs)
 }
 
 /* Exported for geometry tests: segment list of the equidistant ray j. */
-int lo_paths_1d(int K, const double *R, int n_rays, int j,
+int lo_paths_1d(int K, const double *R, int n_rays, double ray_power, int j,
                 int *cell, double *s, double *cosv)
 {
     const double Rout = R[K - 1];
-    const double p = (j + 0.5) * Rout / n_rays;
+    double p, A;
+    lo_ray_1d(Rout, n_rays, ray_power, j, &p, &A);
     lo_seg1d *segs = (lo_seg1d *)malloc(sizeof(lo_seg1d) * 2 * (K + 1));
     int n = lo_ray_segments_1d(K, R, p, segs);
     for (int i = 0; i < n; i++) { cell[i] = segs[i].cell; s[i] = segs[i].s; cosv[i] = segs[i].cosv; }
@@ -245,14 +259,14 @@ int lo_paths_1d(int K, const double *R, int n_rays, int j,
 
 /* Per-cell sum of A_j s over all rays: the "total length sum(s)" that turns
  * a ray's path length into its share of the cell's emission (Sect. 2). */
-void lo_weights_1d(int K, const double *R, int n_rays, double *W)
+void lo_weights_1d(int K, const double *R, int n_rays, double ray_power, double *W)
 {
     const double Rout = R[K - 1];
     lo_seg1d *segs = (lo_seg1d *)malloc(sizeof(lo_seg1d) * 2 * (K + 1));
     for (int c = 0; c < K; c++) W[c] = 0.0;
     for (int j = 0; j < n_rays; j++) {
-        const double p = (j + 0.5) * Rout / n_rays;
-        const double A = LO_PI * Rout * Rout * ((j + 1.0) * (j + 1.0) - (double)j * j) / ((double)n_rays * n_rays);
+        double p, A;
+        lo_ray_1d(Rout, n_rays, ray_power, j, &p, &A);
         int n = lo_ray_segments_1d(K, R, p, segs);
         for (int i = 0; i < n; i++) W[segs[i].cell] += A * segs[i].s;
     }
@@ -267,13 +281,13 @@ void lo_weights_1d(int K, const double *R, int n_rays, double *W)
 void lo_march_1d(const lo_molecule *m, int K, const double *R,
                  const double *t_kin, const double *sigma_turb,
                  const double *v, int n_ch, double v_min, double dv,
-                 int n_rays, double t_bg, const double *Kp, const double *S,
+                 int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
                  double *SIJ, double *ESC, double *NORM)
 {
     const int T = m->n_lines;
     const double Rout = R[K - 1];
     double *W = (double *)malloc(sizeof(double) * K);
-    lo_weights_1d(K, R, n_rays, W);
+    lo_weights_1d(K, R, n_rays, ray_power, W);
     memset(SIJ, 0, sizeof(double) * T * K);
     memset(ESC, 0, sizeof(double) * T * K);
     memset(NORM, 0, sizeof(double) * K);
@@ -296,8 +310,8 @@ void lo_march_1d(const lo_molecule *m, int K, const double *R,
         lo_seg1d *segs = (lo_seg1d *)malloc(sizeof(lo_seg1d) * 2 * (K + 1));
 #pragma omp for schedule(static)
         for (int j = 0; j < n_rays; j++) {
-            const double p = (j + 0.5) * Rout / n_rays;
-            const double A = LO_PI * Rout * Rout * ((j + 1.0) * (j + 1.0) - (double)j * j) / ((double)n_rays * n_rays);
+            double p, A;
+            lo_ray_1d(Rout, n_rays, ray_power, j, &p, &A);
             for (int t = 0; t < T; t++) {
                 const double nbg = lo_bg_occupation(m->line_nu[t], t_bg);
                 for (int k = 0; k < n_ch; k++) I[t * n_ch + k] = nbg;
@@ -460,7 +474,7 @@ int lo_iterate_1d(const lo_molecule *m, int K, const double *R,
                   const double *n_h2, const double *t_kin,
                   const double *sigma_turb, const double *abundance,
                   const double *v, int n_ch, double v_min, double dv,
-                  int n_rays, double t_bg, int ali, int n_iter,
+                  int n_rays, double ray_power, double t_bg, int ali, int n_iter,
                   double *x, double *dtex)
 {
     const int T = m->n_lines, L = m->n_levels;
@@ -473,7 +487,7 @@ int lo_iterate_1d(const lo_molecule *m, int K, const double *R,
     int bad = 0;
     for (int it = 0; it < n_iter; it++) {
         lo_line_params(m, K, n_h2, abundance, dv, x, Kp, S);
-        lo_march_1d(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, t_bg, Kp, S, SIJ, ESC, NORM);
+        lo_march_1d(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S, SIJ, ESC, NORM);
         bad += lo_se_solve(m, K, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, xn);
         if (dtex) dtex[it] = lo_max_rel_dtex(m, K, x, xn);
         memcpy(x, xn, sizeof(double) * L * K);

@@ -58,11 +58,15 @@ def test_1d_brute_force_sampling(oracle):
         np.testing.assert_allclose(cosv, z0 / r0, atol=1e-12)
 
 
-def test_1d_weights_converge_to_volumes(oracle):
+@pytest.mark.parametrize("ray_power", [1.0, 2.0, 0.7])
+def test_1d_weights_converge_to_volumes(oracle, ray_power):
+    """sum_j A_j s_jk -> shell volume as the rays get denser, for equidistant
+    and power-law impact parameters (Sect. 2.1)."""
     K = 4
     errs = []
     for n_rays in (500, 4000):
         m = LI.cloud1d_two_level(K=K, n_rays=n_rays)
+        m["ray_power"] = ray_power
         R = m["radius"]
         W = oracle.weights_1d(m)
         V = 4.0 / 3.0 * np.pi * (R ** 3 - np.concatenate([[0.0], R[:-1]]) ** 3)
@@ -133,3 +137,31 @@ def test_3d_constant_path_length_exact(oracle, N):
                 assert np.all(dz > 0)
                 np.add.at(tot, cells, dz)
         assert np.all(tot == H)
+
+
+def test_1d_power_law_rays(oracle):
+    """Power-law impact parameters: the annuli tile the projected disk, ray j
+    passes at R ((j + 1/2) / n)^a (so a = 1 is the equidistant default) and
+    concentrates towards the centre for a > 1."""
+    m = LI.cloud1d_two_level(K=8, n_rays=12)
+    R = m["radius"][-1]
+    base = [oracle.paths_1d(m, j) for j in range(12)]
+    m["ray_power"] = 1.0
+    for j in range(12):
+        for u, v in zip(base[j], oracle.paths_1d(m, j)):
+            np.testing.assert_array_equal(u, v)
+    for a in (2.0, 3.0):
+        m["ray_power"] = a
+        for j in range(12):
+            cell, s, _ = oracle.paths_1d(m, j)
+            p = R * ((j + 0.5) / 12) ** a
+            assert s.sum() == pytest.approx(2.0 * np.sqrt(R * R - p * p), rel=1e-13)
+            assert cell.min() == np.searchsorted(m["radius"], p, side="right")
+    # the weights of all rays add up to the volume covered: sum_k W_k = sum_j A_j 2 z_j
+    m["ray_power"] = 2.0
+    W = oracle.weights_1d(m)
+    b = R * (np.arange(13) / 12.0) ** 2.0
+    A = np.pi * (b[1:] ** 2 - b[:-1] ** 2)
+    assert A.sum() == pytest.approx(np.pi * R * R, rel=1e-14)
+    p = R * ((np.arange(12) + 0.5) / 12) ** 2.0
+    assert W.sum() == pytest.approx((A * 2.0 * np.sqrt(R * R - p * p)).sum(), rel=1e-13)

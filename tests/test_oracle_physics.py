@@ -194,11 +194,13 @@ def _beta_sphere(tau_R):
     return integrate.dblquad(f, 0, 1, -1, 1, epsabs=1e-13, epsrel=1e-12)[0]
 
 
-def test_sphere_mean_intensity_matches_escape_probability(oracle):
+@pytest.mark.parametrize("ray_power", [1.0, 1.5])
+def test_sphere_mean_intensity_matches_escape_probability(oracle, ray_power):
     mol = LI.two_level_molecule()
     errs = []
     for n_rays in (1000, 8000):
         m = LI.uniform_sphere(K=4, n_ch=12, n_rays=n_rays, abundance=3e-8, half_width_kms=1.0)
+        m["ray_power"] = ray_power
         x = oracle.lte_populations(mol, m["t_kin"])
         Kp, S = oracle.line_params(mol, m, x)
         SIJ, ESC, NORM = oracle.march_1d(mol, m, Kp, S)
