@@ -67,8 +67,10 @@ typedef struct loc_allocator {
  *               T_ex) are the leaves, in level-ordered cell order.
  *  n_shells     1D: number of concentric shells K >= 1.
  *  radius       1D: [K] outer radii, strictly increasing, > 0.
- *  n_rays       1D: number of equidistant impact parameters
- *               p_j = (j + 1/2) R / n_rays (0 -> n_shells).
+ *  n_rays       1D: number of impact parameters (0 -> n_shells); ray j
+ *               passes at p_j = R ((j + 1/2) / n_rays)^ray_power and stands
+ *               for the annulus between R (j / n_rays)^ray_power and
+ *               R ((j + 1) / n_rays)^ray_power (Sect. 2.1).
  *  n_root, h0   3D: N^3 root cells of size h0 (cm), 1 <= N <= 255; cells
  *               are indexed x fastest: idx = (iz N + iy) N + ix.
  *  n_dir, dirs  3D: [n_dir][3] unit ray directions (e.g. HEALPix centres).
@@ -91,6 +93,10 @@ typedef struct loc_allocator {
  *  t_bg         background (CMB) temperature of the entering rays.
  *  stream       cudaStream_t to queue all work on (NULL: legacy default).
  *  allocator    optional device allocator (NULL: cudaMalloc / cudaFree).
+ *  ray_power    1D: exponent of the impact-parameter power law; 0 or 1 give
+ *               equidistant rays (the default), > 1 concentrates rays towards
+ *               the centre (small inner shells), (0, 1) towards the edge;
+ *               at most 10.
  */
 typedef struct loc_model_desc {
     int geometry;
@@ -112,6 +118,7 @@ typedef struct loc_model_desc {
     double t_bg;
     void *stream;
     const loc_allocator *allocator;
+    double ray_power;
 } loc_model_desc;
 
 /*

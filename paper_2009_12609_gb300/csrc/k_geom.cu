@@ -1,8 +1,9 @@
 // k_geom.cu -- ray geometry set-up kernels.
 //
 // 1D (Sect. 2.1): concentric shells with outer radii R_k, parallel rays with
-// equidistant impact parameters p_j = (j + 1/2) R / n_rays, each standing for
-// the annulus of area A_j = pi R^2 ((j+1)^2 - j^2) / n_rays^2.  A ray visits
+// impact parameters p_j = R ((j + 1/2) / n_rays)^a, each standing for the
+// annulus between R (j / n_rays)^a and R ((j + 1) / n_rays)^a (a = 1, the
+// default, gives equidistant rays and A_j = pi R^2 ((j+1)^2 - j^2) / n_rays^2).  A ray visits
 // shells K-1 .. t+1, its tangent shell t (smallest k with R_k > p) in two
 // halves, then t+1 .. K-1; step lengths are differences of
 // sqrt(R_k^2 - p^2).  The path lengths are precomputed once (the paper does
@@ -20,15 +21,23 @@
 
 namespace loc {
 
+// ray j passes at p_j = R ((j + 1/2) / n)^a and stands for the annulus
+// between R (j / n)^a and R ((j + 1) / n)^a (a = 1: equidistant rays)
 __device__ __forceinline__ double ray_p(const DevModel &m, int j)
 {
-    return (j + 0.5) * m.radius[m.K - 1] / m.n_rays;
+    const double R = m.radius[m.K - 1];
+    if (!(m.ray_power > 0.0) || m.ray_power == 1.0) return (j + 0.5) * R / m.n_rays;
+    return R * pow((j + 0.5) / m.n_rays, m.ray_power);
 }
 
 __device__ __forceinline__ double ray_area(const DevModel &m, int j)
 {
     const double R = m.radius[m.K - 1];
-    return kPI * R * R * ((j + 1.0) * (j + 1.0) - (double)j * j) / ((double)m.n_rays * m.n_rays);
+    if (!(m.ray_power > 0.0) || m.ray_power == 1.0)
+        return kPI * R * R * ((j + 1.0) * (j + 1.0) - (double)j * j) / ((double)m.n_rays * m.n_rays);
+    const double b0 = R * pow((double)j / m.n_rays, m.ray_power);
+    const double b1 = R * pow((j + 1.0) / m.n_rays, m.ray_power);
+    return kPI * (b1 * b1 - b0 * b0);
 }
 
 __device__ __forceinline__ int tangent_shell(const DevModel &m, double p)

@@ -158,6 +158,9 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         D.K = K;
         D.n_rays = d->n_rays > 0 ? d->n_rays : K;
         CHECK(D.n_rays <= (1 << 16), "n_rays must be <= 65536");
+        CHECK(d->ray_power == 0.0 || (d->ray_power > 0.0 && d->ray_power <= 10.0),
+              "ray_power must be 0 (equidistant) or in (0, 10]");
+        D.ray_power = d->ray_power > 0.0 ? d->ray_power : 1.0;
     } else if (d->geometry == LOC_GRID_3D) {
         CHECK(d->n_root >= 1 && d->n_root <= 255, "n_root must be in [1, 255]");
         CHECK(d->h0 > 0.0 && std::isfinite(d->h0), "h0 must be > 0");

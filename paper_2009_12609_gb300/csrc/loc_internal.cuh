@@ -61,6 +61,7 @@ struct DevModel {
 
     // 1D geometry
     int K, n_rays;
+    double ray_power;                   // impact parameters R ((j + 1/2) / n_rays)^ray_power (<= 0: 1)
     long long n_segs;
     double *radius;                     // [K]
     float *v1d;                         // [K] radial velocity

@@ -49,6 +49,7 @@ struct ArenaLayout {
 struct Request {
     uint64_t ticket = 0;
     int K = 0, n_rays = 0, n_ch = 0;
+    double ray_power = 1.0;
     double v_min = 0, dv = 0, t_bg = 0;
     int L = 0, T = 0, P = 0;
     double mass = 0;
@@ -265,6 +266,7 @@ static bool admit(loc_server *s, int si, Request *q)
     m.inv_s2sig = (float *)(b + a.inv);
     m.K = q->K;
     m.n_rays = q->n_rays;
+    m.ray_power = q->ray_power;
     m.radius = (double *)(b + a.radius);
     m.v1d = (float *)(b + a.v1d);
     m.ray_off = (int *)(b + a.ray_off);
@@ -326,7 +328,8 @@ static bool admit(loc_server *s, int si, Request *q)
     const double Rout = R[q->K - 1];
     long long tot = 0;
     for (int j = 0; j < q->n_rays; j++) {
-        const double p = (j + 0.5) * Rout / q->n_rays;
+        const double p = (q->ray_power == 1.0) ? (j + 0.5) * Rout / q->n_rays
+                                               : Rout * std::pow((j + 0.5) / q->n_rays, q->ray_power);
         const int t = (int)(std::upper_bound(R, R + q->K, p) - R);
         h.ray_steps[j] = (t < q->K) ? 2 * (q->K - t) : 0;
         tot += h.ray_steps[j];
@@ -511,7 +514,8 @@ loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_m
         }
     }
     const int n_rays = d->n_rays > 0 ? d->n_rays : K;
-    if (n_rays > 4096 || d->n_ch < 1 || d->n_ch > kMaxChannels || !(d->dv > 0.0)) {
+    if (n_rays > 4096 || d->n_ch < 1 || d->n_ch > kMaxChannels || !(d->dv > 0.0) ||
+        !(d->ray_power == 0.0 || (d->ray_power > 0.0 && d->ray_power <= 10.0))) {
         set_error("1D model: bad ray count or channel grid");
         return LOC_EINVAL;
     }
@@ -544,6 +548,7 @@ loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_m
     if (!q) { set_error("host allocation failed"); return LOC_ENOMEM; }
     q->K = K;
     q->n_rays = n_rays;
+    q->ray_power = d->ray_power > 0.0 ? d->ray_power : 1.0;
     q->n_ch = d->n_ch;
     q->v_min = d->v_min;
     q->dv = d->dv;

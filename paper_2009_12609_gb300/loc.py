@@ -55,7 +55,7 @@ class loc_model_desc(ctypes.Structure):
                 ("v", _d), ("vx", _d), ("vy", _d), ("vz", _d),
                 ("n_ch", ctypes.c_int), ("v_min", ctypes.c_double), ("dv", ctypes.c_double),
                 ("t_bg", ctypes.c_double), ("stream", _vp),
-                ("allocator", ctypes.POINTER(loc_allocator))]
+                ("allocator", ctypes.POINTER(loc_allocator)), ("ray_power", ctypes.c_double)]
 
 
 class loc_molecule_desc(ctypes.Structure):
@@ -235,6 +235,7 @@ def model_desc(model, keep, stream=None, allocator=None):
         d.n_shells = len(model["radius"])
         d.radius = _pd(keep(_f64(model["radius"])))
         d.n_rays = int(model.get("n_rays", 0) or 0)
+        d.ray_power = float(model.get("ray_power", 0.0) or 0.0)
         d.v = _pd(keep(_f64(model["v"])))
     elif geo in ("grid3d", "octree3d"):
         d.geometry = LOC_GRID_3D if geo == "grid3d" else LOC_OCTREE_3D

@@ -233,3 +233,31 @@ def test_duplicate_level_pairs_rejected(loc):
             assert e.value.status == loc.LOC_EINVAL
         m.set_molecule(rot)
         m.iterate(max_iter=1)
+
+
+@pytest.mark.parametrize("ray_power,steps_per_chunk", [(2.0, -1), (2.0, 16), (0.6, 0)])
+def test_power_law_rays_match_oracle(loc, oracle, ray_power, steps_per_chunk):
+    """Impact parameters following a power law (Sect. 2.1): ray geometry,
+    weights, one ray simulation and the ALI iterations agree with the oracle;
+    whole rays and runs of steps alike."""
+    mol = LI.rotor_molecule(n_levels=6)
+    model = LI.cloud1d_rotor(K=40, n_ch=96)
+    model["n_rays"] = 60
+    model["ray_power"] = ray_power
+    with loc.Model(model, mol) as m:
+        m.march(window_sigmas=8.0, steps_per_chunk=steps_per_chunk)
+        sij, esc, norm = m.radiation()
+        x = oracle.lte_populations(mol, model["t_kin"])
+        Kp, S = oracle.line_params(mol, model, x)
+        rs, re_, rn = oracle.march_1d(mol, model, Kp, S)
+        np.testing.assert_allclose(norm, rn, rtol=2e-5)
+        np.testing.assert_allclose(sij, rs, rtol=5e-5, atol=1e-7 * np.abs(rs).max())
+        np.testing.assert_allclose(esc, re_, rtol=5e-5, atol=1e-7 * np.abs(re_).max())
+        m.reset()
+        m.iterate(max_iter=12, window_sigmas=8.0, steps_per_chunk=steps_per_chunk)
+        x_ref, _ = oracle.iterate_1d(mol, model, 12)
+        assert _tex_err(mol, x_ref, m, oracle) < 1e-4
+    bad = dict(model)
+    bad["ray_power"] = -1.0
+    with pytest.raises(loc.LocError):
+        loc.Model(bad, mol)

@@ -1,0 +1,109 @@
+"""1D versus 3D self-consistency (the pattern of the paper's comparison of
+its 1D and 3D codes on one spherical cloud, Sect. 3.2, without hyperfine
+structure): the same Gaussian core with slow infall is solved on 1D shells
+and on a regular 3D grid, and the excitation temperatures (by radius) and
+the emergent central spectrum agree within the 5 % the paper reports
+between its geometries.
+
+The 3D box is four cloud radii wide and empty outside the sphere, so every
+line of sight of the periodic grid meets the cloud (or one periodic image
+of it) at most once, as in the 1D model.  Both sides run on the GPU; the
+grid uses the 48 HEALPix directions, the map a direction along +z.
+"""
+import numpy as np
+import pytest
+
+import loc_inputs as LI
+
+pytestmark = pytest.mark.gpu
+
+PC = 3.0856775814913673e18
+KMS = 1.0e5
+
+
+@pytest.fixture(scope="module")
+def loc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_12609_gb300 import build, loc as L
+    build.build()
+    L.load()
+    return L
+
+
+R = 0.1 * PC
+N_CH, HALF = 64, 1.5            # channels over +-1.5 km/s
+
+
+def _n(r):
+    return np.where(r < R, 3.0e4 * np.exp(-0.5 * (r / (0.5 * R)) ** 2), 0.0)
+
+
+def _v(r):
+    return -0.2 * KMS * np.minimum(r / R, 1.0)
+
+
+def _cloud_1d(K=48):
+    k = np.arange(K, dtype=np.float64)
+    r_mid = (k + 0.5) * R / K
+    dv = 2 * HALF * KMS / N_CH
+    return dict(geometry="shells1d", radius=(k + 1.0) * R / K, n_h2=_n(r_mid),
+                t_kin=np.full(K, 15.0), sigma_turb=np.full(K, 0.2 * KMS),
+                abundance=np.full(K, 3e-9), v=_v(r_mid), n_ch=N_CH, v_min=-HALF * KMS, dv=dv,
+                n_rays=4 * K, t_bg=2.73)
+
+
+def _cloud_3d(N=96, dirs=None):
+    L = 4.0 * R
+    h = L / N
+    c = (np.arange(N) + 0.5) * h - 0.5 * L
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    # x fastest: idx = (iz N + iy) N + ix
+    X, Y, Z = (a.transpose(2, 1, 0).reshape(-1) for a in (X, Y, Z))
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    vr = _v(r)
+    rr = np.maximum(r, 1e-30)
+    nc = N ** 3
+    return dict(geometry="grid3d", n_root=N, h0=h, n_h2=_n(r), t_kin=np.full(nc, 15.0),
+                sigma_turb=np.full(nc, 0.2 * KMS), abundance=np.full(nc, 3e-9),
+                vx=vr * X / rr, vy=vr * Y / rr, vz=vr * Z / rr,
+                dirs=LI.healpix_ring_directions(2) if dirs is None else dirs,
+                n_ch=N_CH, v_min=-HALF * KMS, dv=2 * HALF * KMS / N_CH, t_bg=2.73), r
+
+
+def test_1d_and_3d_agree_on_a_spherical_core(loc):
+    mol = LI.rotor_molecule(n_levels=5)
+    m1 = _cloud_1d()
+    m3, r3 = _cloud_3d()
+    n_iter = 25
+    with loc.Model(m1, mol) as a:
+        a.iterate(max_iter=n_iter, window_sigmas=8.0)
+        tex1 = [a.tex(t) for t in range(2)]
+        K = len(m1["radius"])
+        h3 = m3["h0"]
+        # central lines of sight of the 3D map along +z pass at p = h / sqrt(2)
+        p_c = h3 / np.sqrt(2.0)
+        spec1 = a.spectra(0, [p_c])[0]
+    with loc.Model(m3, mol) as b:
+        b.iterate(max_iter=n_iter, window_sigmas=8.0)
+        x3 = b.populations()
+        tex3 = [b.tex(t) for t in range(2)]
+    r_mid = (np.arange(K) + 0.5) * R / K
+    inside = r3 < 0.9 * R
+    for t in range(2):
+        ref = np.interp(r3[inside], r_mid, tex1[t])
+        rel = np.abs(tex3[t][inside] / ref - 1.0)
+        assert np.median(rel) < 0.02, (t, np.median(rel))
+        assert np.percentile(rel, 95) < 0.05, (t, np.percentile(rel, 95))
+    # emergent spectrum through the centre: 1D spectrum vs the 3D map pixel
+    m3z, _ = _cloud_3d(dirs=np.array([[0.0, 0.0, 1.0]]))
+    with loc.Model(m3z, mol) as c:
+        c.set_populations(x3)
+        T = c.map3d(0, 0).reshape(m3z["n_root"], m3z["n_root"], -1)
+    N = m3z["n_root"]
+    spec3 = T[N // 2, N // 2]
+    peak1, peak3 = np.abs(spec1).max(), np.abs(spec3).max()
+    assert peak1 > 0.02, peak1                 # a clearly detected line (K)
+    assert abs(peak3 / peak1 - 1.0) < 0.05, (peak1, peak3)
+    assert np.abs(spec3 - spec1).max() < 0.08 * peak1, np.abs(spec3 - spec1).max() / peak1
