@@ -52,6 +52,19 @@ __device__ __forceinline__ long long cross_z(long long target, long long q, unsi
 
 __device__ __forceinline__ long long fq(long long q, long long z) { return (q * z) >> kFixedBits; }
 
+// A lattice coordinate A = A0 + floor(q z / 2^F) reduced modulo the model
+// width E: A0 < E (line offset) and floor(q z / 2^F) <= z < E (slope <= 1),
+// so A < 2 E and one conditional subtraction replaces a 64-bit division.
+__device__ __forceinline__ long long wrap_e(long long A, long long E) { return A >= E ? A - E : A; }
+
+// v mod M in [0, M) for v within a few M of that range (no 64-bit division)
+__device__ __forceinline__ long long mod_near(long long v, long long M)
+{
+    while (v < 0) v += M;
+    while (v >= M) v -= M;
+    return v;
+}
+
 struct OctGeo {
     Dir3D D;
     long long E, o;
@@ -62,8 +75,8 @@ __device__ __forceinline__ void oct_point(const OctGeo &g, long long Au, long lo
 {
     long long mm[3];
     mm[g.D.m] = z;
-    mm[g.D.a] = Au % g.E;
-    mm[g.D.b] = Bu % g.E;
+    mm[g.D.a] = wrap_e(Au, g.E);
+    mm[g.D.b] = wrap_e(Bu, g.E);
 #pragma unroll
     for (int ax = 0; ax < 3; ax++) p[ax] = g.D.flip[ax] ? g.E - 1 - mm[ax] : mm[ax];
 }
@@ -166,11 +179,11 @@ __device__ __forceinline__ void oct_spawn(const DevModel &m, const OctGeo &g, co
     const long long da = fq(g.D.qa, zf + H - 1) - fa, db = fq(g.D.qb, zf + H - 1) - fb;
     const long long Mc = (long long)g.N << (k + 1);
     // first candidate index along each axis: lattice position >= box lower bound - drift
-    long long xa = (ma0 - da - g.o - fa) % g.E;
-    if (xa < 0) xa += g.E;
-    long long xb = (mb0 - db - g.o - fb) % g.E;
-    if (xb < 0) xb += g.E;
-    const long long ia0 = (xa + Hc - 1) / Hc, jb0 = (xb + Hc - 1) / Hc;
+    // (ma0, fa < E; da <= H, o < H0 <= E: the argument lies in (-3E, E))
+    const long long xa = mod_near(ma0 - da - g.o - fa, g.E);
+    const long long xb = mod_near(mb0 - db - g.o - fb, g.E);
+    const int shc = kFixedBits - k - 1;                 // Hc = 2^shc
+    const long long ia0 = (xa + Hc - 1) >> shc, jb0 = (xb + Hc - 1) >> shc;
     bool is_new = false;
     int ci = 0, cj = 0;
     long long zin = 0;
@@ -179,17 +192,15 @@ __device__ __forceinline__ void oct_spawn(const DevModel &m, const OctGeo &g, co
     const int nu = (int)min(5ll, Mc);
     const int cu = lane / 5, cv = lane % 5;
     if (lane < 25 && cu < nu && cv < nu) {
-        ci = (int)((ia0 + cu) % Mc);
-        cj = (int)((jb0 + cv) % Mc);
+        ci = (int)mod_near(ia0 + cu, Mc);               // ia0 <= Mc: at most Mc + 4
+        cj = (int)mod_near(jb0 + cv, Mc);
         if ((ci & 1) || (cj & 1)) {                      // creation level k + 1
             const long long A0 = g.o + (long long)ci * Hc, B0 = g.o + (long long)cj * Hc;
             // offset from the box's lower bound: [0, H) inside, otherwise taken
             // as before the box (the line may still drift into it)
-            long long ar = (A0 + fa - ma0) % g.E;
-            if (ar < 0) ar += g.E;
+            long long ar = mod_near(A0 + fa - ma0, g.E);     // argument in (-E, 2E)
             if (ar >= H) ar -= g.E;
-            long long br = (B0 + fb - mb0) % g.E;
-            if (br < 0) br += g.E;
+            long long br = mod_near(B0 + fb - mb0, g.E);
             if (br >= H) br -= g.E;
             const long long NEVER = 1ll << 62;
             bool ok = (ar >= -da) && (ar < H) && (br >= -db) && (br < H);
@@ -307,11 +318,11 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
             const long long HL = H0 >> Lc;
             long long zn = oct_mlo(g, g.D.m, p[g.D.m], Lc) + HL;
             if (g.D.qa > 0) {
-                const long long T = Au - (Au % g.E) + oct_mlo(g, g.D.a, p[g.D.a], Lc) + HL;
+                const long long T = Au - wrap_e(Au, g.E) + oct_mlo(g, g.D.a, p[g.D.a], Lc) + HL;
                 zn = min(zn, cross_z(T - (Au - fq(g.D.qa, cur.z)), g.D.qa, g.D.ma));
             }
             if (g.D.qb > 0) {
-                const long long T = Bu - (Bu % g.E) + oct_mlo(g, g.D.b, p[g.D.b], Lc) + HL;
+                const long long T = Bu - wrap_e(Bu, g.E) + oct_mlo(g, g.D.b, p[g.D.b], Lc) + HL;
                 zn = min(zn, cross_z(T - (Bu - fq(g.D.qb, cur.z)), g.D.qb, g.D.mb));
             }
             zn = min(zn, g.E);
@@ -494,11 +505,11 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) map_octree_kernel(DevM
         const long long HL = H0 >> Lc;
         long long zn = oct_mlo(g, g.D.m, p[g.D.m], Lc) + HL;
         if (g.D.qa > 0) {
-            const long long T = Au - (Au % g.E) + oct_mlo(g, g.D.a, p[g.D.a], Lc) + HL;
+            const long long T = Au - wrap_e(Au, g.E) + oct_mlo(g, g.D.a, p[g.D.a], Lc) + HL;
             zn = min(zn, cross_z(T - A0, g.D.qa, g.D.ma));
         }
         if (g.D.qb > 0) {
-            const long long T = Bu - (Bu % g.E) + oct_mlo(g, g.D.b, p[g.D.b], Lc) + HL;
+            const long long T = Bu - wrap_e(Bu, g.E) + oct_mlo(g, g.D.b, p[g.D.b], Lc) + HL;
             zn = min(zn, cross_z(T - B0, g.D.qb, g.D.mb));
         }
         zn = min(zn, g.E);
