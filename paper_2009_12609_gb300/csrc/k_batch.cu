@@ -66,7 +66,7 @@ batch_march_kernel(BatchSlot *slots, const int4 *items, const int *n_items, unsi
         a0.per = S->per;
         a0.n_groups = S->n_groups;
         a0.window = window;
-        a0.inv_dv = (float)(1.0 / m.dv);
+        a0.inv_dv = S->inv_dv;
         a0.fp64_acc = 0;
         a0.count = 0;
         const MarchArgs a = warp_args(m, a0, w.z);

@@ -15,6 +15,7 @@ struct BatchSlot {
     float tol, last_dtex;
     int ali;
     int per, n_groups;   // lines per warp, line groups
+    float inv_dv;        // 1 / channel width in FP32
 };
 
 // Line-group classes of the batched march (compile-time group sizes) and

@@ -112,8 +112,8 @@ __device__ __forceinline__ void step_window(const DevModel &m, const MarchArgs &
                                             float &u0, float &db, int &klo, int &khi)
 {
     const int nch = m.n_ch;
-    u0 = ((float)m.v_min + st.vlos) * a.inv_dv;
-    db = (float)m.dv * st.inv;
+    u0 = (m.vmin_f + st.vlos) * a.inv_dv;
+    db = m.dv_f * st.inv;
     klo = 0;
     khi = nch;
     if (a.window > 0.f) {

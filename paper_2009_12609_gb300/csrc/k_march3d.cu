@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m
         const float4 cv = m.vel[st.cell];
         st.vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
         st.inv = cv.w;
-        st.s = (float)dz * D.unit;
-        st.w = (float)dz * wscale;
+        st.s = (float)(int)dz * D.unit;             // dz <= one cell = 2^24 units
+        st.w = (float)(int)dz * wscale;
         load_lines<G>(m, a, st);
     };
     long long nw = 0;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) map_grid3d_kernel(DevMode
         const float4 cv = m.vel[cell];
         const float vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
         const float2 ks = m.ks[cell * m.T + t];
-        los_step<CMAX>(dI, nchunk, lane, ks.x * ((float)dz * D.unit), ks.y - nb, (vmin + vlos) * inv_dv,
+        los_step<CMAX>(dI, nchunk, lane, ks.x * ((float)(int)dz * D.unit), ks.y - nb, (vmin + vlos) * inv_dv,
                        dv * cv.w);
         if (wk.done(m.N)) break;
     }

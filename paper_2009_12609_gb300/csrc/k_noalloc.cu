@@ -133,7 +133,9 @@ extern "C" loc_status loc_radiation1d_noalloc(int n_shells, int n_rays, const do
     m.n_cells = K;
     m.n_ch = n_ch;
     m.v_min = v_min;
+    m.vmin_f = (float)v_min;
     m.dv = dv;
+    m.dv_f = (float)dv;
     m.K = K;
     m.n_rays = n_rays;
     m.radius = (double *)radius;

@@ -334,8 +334,8 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                 const float4 cv = m.vel[leaf];
                 st.vlos = cv.x * g.D.d[0] + cv.y * g.D.d[1] + cv.z * g.D.d[2];
                 st.inv = cv.w;
-                st.s = (float)dz * g.D.unit;
-                st.w = (float)dz / (float)HL * wscale;
+                st.s = (float)(int)dz * g.D.unit;       // dz <= one leaf <= 2^24 units
+                st.w = (float)(int)dz / (float)(int)HL * wscale;
                 load_lines<G>(m, a, st);
                 nw += (long long)march_step<G>(m, a, I, st, lane) * a.n_lines;
                 __syncwarp();
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) map_octree_kernel(DevM
         const float4 cv = m.vel[leaf];
         const float vlos = cv.x * g.D.d[0] + cv.y * g.D.d[1] + cv.z * g.D.d[2];
         const float2 ks = m.ks[(long long)leaf * m.T + t];
-        los_step<CMAX>(dI, nchunk, lane, ks.x * ((float)(zn - z) * g.D.unit), ks.y - nb,
+        los_step<CMAX>(dI, nchunk, lane, ks.x * ((float)(int)(zn - z) * g.D.unit), ks.y - nb,
                        (vmin + vlos) * inv_dv, dv * cv.w);
         z = zn;
     }

@@ -37,9 +37,14 @@ __global__ void lte_kernel(DevModel m)
     for (int i = 0; i < m.L; i++) x[i] /= z;
 }
 
+// FP64 elementwise kernels of small models run in 32-thread blocks so that
+// their warps spread over the SMs' FP64 pipes
+static int fp64_block(long long n) { return n <= 152ll * 256 ? 32 : 256; }
+
 loc_status launch_lte(const DevModel &m, cudaStream_t st)
 {
-    lte_kernel<<<(unsigned)((m.n_cells + 255) / 256), 256, 0, st>>>(m);
+    const int bs = fp64_block(m.n_cells);
+    lte_kernel<<<(unsigned)((m.n_cells + bs - 1) / bs), bs, 0, st>>>(m);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }
@@ -87,7 +92,8 @@ __global__ void line_params_kernel(DevModel m, int zero_acc)
 loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc)
 {
     const long long n = (long long)m.T * m.n_cells;
-    line_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, zero_acc);
+    const int bs = fp64_block(n);
+    line_params_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(m, zero_acc);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(kSeWarps * 32) se_kernel(DevModel m, int ali, 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int seg = lane / LW, sl = lane - seg * LW;
     double *M = se_smem + (size_t)(wid * CPW + seg) * SEG;
-    const long long c0 = ((long long)blockIdx.x * kSeWarps + wid) * CPW;
+    const long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + wid) * CPW;
     if (c0 >= m.n_cells) return;                    // whole warp
     long long c = c0 + seg;
     const bool valid = c < m.n_cells;
@@ -209,11 +215,21 @@ static loc_status launch_se_l(const DevModel &m, int ali, int fp64_acc, cudaStre
         return LOC_OK;
     }
     constexpr int CPW = 32 / LMAX;
-    const size_t smem = sizeof(double) * kSeWarps * CPW * (LMAX * (LMAX + 2) + LMAX);
+    // the FP64 pipes are per SM: a small model spreads its warps one per
+    // block (one per SM) instead of packing kSeWarps warps on fewer SMs
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    const long long warps = (m.n_cells + CPW - 1) / CPW;
+    const int wpb = (warps <= 2ll * nsm) ? 1 : kSeWarps;
+    const size_t smem = sizeof(double) * wpb * CPW * (LMAX * (LMAX + 2) + LMAX);
     LOC_CUDA_TRY(cudaFuncSetAttribute(se_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long cells_per_block = (long long)kSeWarps * CPW;
+    const long long cells_per_block = (long long)wpb * CPW;
     const unsigned nb = (unsigned)((m.n_cells + cells_per_block - 1) / cells_per_block);
-    se_kernel<LMAX><<<nb, kSeWarps * 32, smem, st>>>(m, ali, fp64_acc);
+    se_kernel<LMAX><<<nb, wpb * 32, smem, st>>>(m, ali, fp64_acc);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

@@ -142,6 +142,8 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
     D.n_ch = d->n_ch;
     D.v_min = d->v_min;
     D.dv = d->dv;
+    D.vmin_f = (float)d->v_min;
+    D.dv_f = (float)d->dv;
     D.t_bg = d->t_bg;
     CHECK(d->n_ch >= 1 && d->n_ch <= kMaxChannels, "n_ch must be in [1, %d], got %d", kMaxChannels, d->n_ch);
     CHECK(std::isfinite(d->v_min) && d->dv > 0.0 && std::isfinite(d->dv), "channel grid: need finite v_min and dv > 0");

@@ -52,6 +52,7 @@ struct DevModel {
     long long n_cells;
     int n_ch;
     double v_min, dv;
+    float vmin_f, dv_f;                 // the channel grid in FP32 (the march uses no FP64)
     double t_bg;
 
     // static per-cell data

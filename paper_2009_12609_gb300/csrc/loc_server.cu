@@ -259,6 +259,8 @@ static bool admit(loc_server *s, int si, Request *q)
     m.n_ch = q->n_ch;
     m.v_min = q->v_min;
     m.dv = q->dv;
+    m.vmin_f = (float)q->v_min;
+    m.dv_f = (float)q->dv;
     m.t_bg = q->t_bg;
     m.n_h2 = (double *)(b + a.n_h2);
     m.t_kin = (double *)(b + a.t_kin);
@@ -313,6 +315,7 @@ static bool admit(loc_server *s, int si, Request *q)
     bs.ali = q->ali;
     bs.per = per;
     bs.n_groups = (q->T + per - 1) / per;
+    bs.inv_dv = (float)(1.0 / q->dv);
     if (cudaMemcpyAsync(s->slots_d + si, &bs, sizeof(bs), cudaMemcpyHostToDevice, s->st) != cudaSuccess)
         return false;
     if (cudaStreamSynchronize(s->st) != cudaSuccess) return false;    // bs leaves scope
