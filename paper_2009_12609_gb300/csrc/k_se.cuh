@@ -63,7 +63,7 @@ __device__ __forceinline__ double2 coll_rate(const DevModel &m, long long c, int
 // columns and the right-hand side), F: LMAX scratch, both in shared memory
 // and owned by the segment.  With valid == false the segment repeats the work
 // of a real cell but stores nothing.  Returns this lane's part of the
-// convergence metric.
+// convergence metric (0 when want_dtex is false).
 //
 // Balance of level i: sum_j x_j R(j -> i) - x_i sum_j R(i -> j) = 0, i.e.
 // M[i][j] = R(j -> i) off the diagonal and M[i][i] = -sum_j M[j][i].  Each
@@ -74,7 +74,8 @@ __device__ __forceinline__ double2 coll_rate(const DevModel &m, long long c, int
 // substitution with lanes over rows, one broadcast per unknown.
 template <int LMAX, int LW>
 __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, bool valid, int ali,
-                                             int fp64_acc, int sl, double *M, double *F)
+                                             int fp64_acc, int sl, double *M, double *F,
+                                             bool want_dtex = true)
 {
     constexpr int W = LMAX + 2;
     const int L = m.L;
@@ -168,7 +169,7 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
     }
     __syncwarp();
     float my_d = 0.f;
-    if (valid) {
+    if (valid && want_dtex) {
         const double *xo = m.x + c * L;
         for (int t = sl; t < m.T; t += LW) {
             if (F[m.line_u[t]] < 1e-6) continue;

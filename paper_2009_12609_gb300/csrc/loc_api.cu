@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "loc_internal.cuh"
 
 namespace loc {
@@ -741,14 +743,28 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     float dtex = 0.f;
     bool converged = false;
     loc_status st = LOC_OK;
+    // NVTX ranges mark the host-side phases of every iteration for timeline
+    // tools (no cost without an attached tool)
+    nvtxRangePushA("loc_iterate");
     for (it = 0; it < o->max_iter; it++) {
         const size_t b = 4 * (size_t)it;
         if (mark(b) != cudaSuccess) { st = LOC_ECUDA; break; }
-        if ((st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1)) != LOC_OK) break;
+        nvtxRangePushA("line parameters");
+        st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1);
+        nvtxRangePop();
+        if (st != LOC_OK) break;
         if (mark(b + 1) != cudaSuccess) { st = LOC_ECUDA; break; }
-        if ((st = march_impl(m, o, true)) != LOC_OK) break;
+        nvtxRangePushA("ray march");
+        st = march_impl(m, o, true);
+        nvtxRangePop();
+        if (st != LOC_OK) break;
         if (mark(b + 2) != cudaSuccess) { st = LOC_ECUDA; break; }
-        if ((st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st)) != LOC_OK) break;
+        // the metric is read when a tolerance is set, and after the last iteration
+        const int want = (o->tol_tex > 0.0 || it == o->max_iter - 1) ? 1 : 0;
+        nvtxRangePushA("statistical equilibrium");
+        st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st, want);
+        nvtxRangePop();
+        if (st != LOC_OK) break;
         if (mark(b + 3) != cudaSuccess) { st = LOC_ECUDA; break; }
         std::swap(D.x, D.x_new);
         if (o->tol_tex > 0.0 || it == o->max_iter - 1) {
@@ -763,6 +779,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
             if (o->tol_tex > 0.0 && dtex < o->tol_tex) { converged = true; it++; break; }
         }
     }
+    nvtxRangePop();
     if (st == LOC_ECUDA && g_err[0] == 0) set_error("CUDA error in the iteration: %s", cudaGetErrorString(cudaGetLastError()));
     cudaEventRecord(e1, m->st);
     cudaError_t ce = cudaEventSynchronize(e1);

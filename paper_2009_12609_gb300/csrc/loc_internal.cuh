@@ -168,7 +168,8 @@ loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st
 loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d_ranges(const DevModel &m, const MarchArgs &a, int *max_w_dev, cudaStream_t st);
 loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
-loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st);
+// want_dtex = 0: skip the convergence metric (nothing reads it this iteration)
+loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st, int want_dtex = 1);
 loc_status launch_lte(const DevModel &m, cudaStream_t st);
 loc_status launch_coll_rates(const DevModel &m, double2 *out, cudaStream_t st);
 loc_status launch_bg(const DevModel &m, cudaStream_t st);

@@ -29,6 +29,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "k_batch.cuh"
 
 using Clock = std::chrono::steady_clock;
@@ -427,7 +429,10 @@ static void server_loop(loc_server *s)
         }
         if (s->need_capture && !capture_graph(s)) { server_fail(s, LOC_ECUDA, "graph capture failed"); return; }
         // 3. k iterations of every active slot
-        if (cudaGraphLaunch(s->graph, s->st) != cudaSuccess ||
+        nvtxRangePushA("server round");
+        const bool round_ok = cudaGraphLaunch(s->graph, s->st) == cudaSuccess;
+        nvtxRangePop();
+        if (!round_ok ||
             cudaMemcpyAsync(s->done_h, s->done_d, sizeof(int) * s->slots.size(), cudaMemcpyDeviceToHost, s->st) != cudaSuccess ||
             cudaStreamSynchronize(s->st) != cudaSuccess) {
             char msg[256];
