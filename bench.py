@@ -318,7 +318,7 @@ def run_gpu(args, wl):
     is1d = model["geometry"] == "shells1d"
     R = model["radius"][-1] if is1d else None
     p_spec = np.concatenate([[0.0], (np.arange(model["n_rays"]) + 0.5) * R / model["n_rays"]]) if is1d else None
-    opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW)
+    opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW, level_cutoff=args.level_cutoff)
     tune_opts = dict(window_sigmas=WINDOW)
 
     m = loc.Model(model, mol)
@@ -449,6 +449,7 @@ def run_gpu(args, wl):
                 "config": {"workload": wl["name"], "iterations_per_step": iters,
                            "ray_steps_per_iteration": seg, "channels": nch, "lines": T,
                            "window_sigmas": WINDOW, "models_per_step": world,
+                           "level_cutoff": args.level_cutoff,
                            "lines_per_warp": tuned_per,
                            "steps_per_chunk": tuned_chunk,
                            "parallelism": f"replicas x{world}" if world > 1 else "single",
@@ -482,6 +483,7 @@ def run_serve(args):
     loc.load()
     n = args.requests
     tol, max_iter = 1e-4, 300
+    cut = args.level_cutoff
     reqs = LI.serving_requests(n=n)
     mols = {L: LI.rotor_molecule(n_levels=L) for L in range(2, 21)}
     srv_opts = dict(max_slots=args.slots, mem_budget_bytes=args.mem_gb << 30,
@@ -495,7 +497,7 @@ def run_serve(args):
     clk.start()
     with loc.Server(**srv_opts) as srv:
         t0 = time.perf_counter()
-        ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol) for r in reqs]
+        ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol, level_cutoff=cut) for r in reqs]
         res = [srv.poll(t, 3600 * 1000)[0] for t in ts]
         closed_s = time.perf_counter() - t0
     clocks = clk.stop()
@@ -513,7 +515,7 @@ def run_serve(args):
             dt = r["arrival_s"] - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            ts.append(srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol))
+            ts.append(srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol, level_cutoff=cut))
         lat = np.array([srv.poll(t, 3600 * 1000)[0]["latency_ms"] for t in ts])
         st = srv.stats()
     # plain per-model path with FP64 accumulation on the same requests (the
@@ -523,12 +525,13 @@ def run_serve(args):
     t0 = time.perf_counter()
     for r in reqs[:n_base]:
         with loc.Model(r["model"], mols[r["n_levels"]]) as m:
-            m.iterate(max_iter=max_iter, tol_tex=tol, precision="fp64acc", window_sigmas=WINDOW)
+            m.iterate(max_iter=max_iter, tol_tex=tol, precision="fp64acc", window_sigmas=WINDOW,
+                      level_cutoff=cut)
     torch.cuda.synchronize()
     base_models_per_s = n_base / (time.perf_counter() - t0)
     with loc.Server(**srv_opts) as srv:
         t0 = time.perf_counter()
-        ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol)
+        ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol, level_cutoff=cut)
               for r in reqs[:n_base]]
         for t in ts:
             srv.poll(t, 3600 * 1000)
@@ -540,7 +543,7 @@ def run_serve(args):
             "config": {"workload": f"serving stream: {n} seeded 1D requests, shells U(32..1024), "
                                    "channels {64,128,256,512}, levels U(2..20), scales x[0.1,10]",
                        "slots": args.slots, "iters_per_launch": 4, "window_sigmas": WINDOW,
-                       "tol_tex": tol, "max_iter": max_iter},
+                       "tol_tex": tol, "max_iter": max_iter, "level_cutoff": cut},
             "converged": conv, "updates_per_s": upd / closed_s,
             "latency_open_loop": {"rate_hz": rate, "requests": n_open,
                                   "p50_ms": float(np.percentile(lat, 50)),
@@ -574,6 +577,8 @@ def main():
                     help="fixed lines per warp instead of the autotuned one (0: autotune)")
     ap.add_argument("--steps-per-chunk", type=int, default=0,
                     help="1D: fixed run length (-1: whole rays) instead of the autotuned one")
+    ap.add_argument("--level-cutoff", type=float, default=0.0,
+                    help="per-cell line truncation: skip lines whose levels hold < this fraction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":

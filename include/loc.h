@@ -168,6 +168,18 @@ typedef struct loc_molecule_desc {
  *                 runs' entering intensities by a scan along the ray);
  *                 c < 0: whole rays, one warp each.  Results equal the
  *                 whole-ray march up to rounding.  Ignored for 3D models.
+ *  level_cutoff   per-cell line truncation in the ALI loop (the paper's
+ *                 suggestion to skip, cell by cell, transitions between
+ *                 levels that are not populated, Sect. 5): 0 = off; c > 0:
+ *                 in a cell where both levels of a line hold less than c of
+ *                 the molecules, the line is left out of that iteration's
+ *                 ray simulation there (its opacity is taken as zero) and
+ *                 the equilibrium solve uses the background intensity with
+ *                 beta = 1 for it.  A ray step whose lines of one pass
+ *                 (lines_per_pass) are all left out is skipped, so the
+ *                 saving grows as lines_per_pass shrinks.  At most 1e-6
+ *                 (below the convergence metric's 1e-6 population floor).
+ *                 Emergent spectra and maps never truncate.
  */
 typedef struct loc_iter_opts {
     int max_iter;
@@ -178,6 +190,7 @@ typedef struct loc_iter_opts {
     double window_sigmas;
     int profile;
     int steps_per_chunk;
+    double level_cutoff;
 } loc_iter_opts;
 
 /* Iteration report. */

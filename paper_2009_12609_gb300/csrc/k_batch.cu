@@ -40,7 +40,8 @@ __global__ void batch_params_kernel(BatchSlot *slots, int n_slots)
     if (s >= n_slots || !slots[s].active) return;
     const DevModel m = slots[s].m;
     const long long n = (long long)m.n_cells * m.T;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) line_params_one(m, i);
+    const double cutoff = slots[s].cutoff;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) line_params_one(m, i, cutoff);
 }
 
 template <int G>

@@ -16,6 +16,7 @@ struct BatchSlot {
     int ali;
     int per, n_groups;   // lines per warp, line groups
     float inv_dv;        // 1 / channel width in FP32
+    double cutoff;       // per-cell line truncation (loc_iter_opts.level_cutoff)
 };
 
 // Line-group classes of the batched march (compile-time group sizes) and

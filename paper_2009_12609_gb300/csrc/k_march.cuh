@@ -133,6 +133,22 @@ __device__ __forceinline__ float step_ks(float K, float s)
     return k;
 }
 
+// Per-cell line truncation marks a line off in a cell with {K, S} = {-0, 0}:
+// K s is then clamped to 1e-20 (step_ks), so the line leaves I unchanged to
+// within 1e-20 relative and its SIJ / ESC are not used by the solve.  A step
+// whose lines are all off in its cell is skipped outright by the warps that
+// do not sum NORM.
+template <int G>
+__device__ __forceinline__ bool lines_off(const DevModel &m, const MarchArgs &a, const Step<G> &st)
+{
+    if (!m.trunc || a.do_norm) return false;
+    bool off = true;
+#pragma unroll
+    for (int t = 0; t < G; t++)
+        off &= (t >= a.n_lines) | (__float_as_uint(st.ks[t].x) == 0x80000000u);
+    return off;
+}
+
 // Narrow windows (at most 16 channels): the lanes take (line, channel) pairs,
 // 32 / Wp lines per chunk with Wp the window rounded up to a power of two.
 // The profile is evaluated once per step (lane c holds channel klo + c), the
@@ -210,11 +226,12 @@ __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchA
 }
 
 // Process one step.  All lanes call it with identical arguments.  Returns
-// the number of channels computed.
+// the number of channels computed (0 for a skipped step).
 template <int G>
 __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
                                           const Step<G> &st, int lane)
 {
+    if (lines_off<G>(m, a, st)) return 0;
     const int nch = m.n_ch;
     float u0, db;
     int klo, khi;
@@ -406,6 +423,7 @@ template <int G>
 __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &a, float *A, float *B,
                                             const Step<G> &st, int lane, int tlo, int thi)
 {
+    if (lines_off<G>(m, a, st)) return;                   // identity map
     float u0, db;
     int klo, khi;
     step_window(m, a, st, u0, db, klo, khi);

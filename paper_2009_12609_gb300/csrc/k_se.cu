@@ -70,11 +70,11 @@ loc_status launch_bg(const DevModel &m, cudaStream_t st)
 // zero_acc: 0 keep the accumulators; 1 (2) also clear the FP32 (FP64)
 // accumulators of entry idx, NORM of its cell and the convergence metric,
 // the start of a ray simulation in the ALI loop
-__global__ void line_params_kernel(DevModel m, int zero_acc)
+__global__ void line_params_kernel(DevModel m, int zero_acc, double cutoff)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)m.T * m.n_cells) return;
-    line_params_one(m, idx);
+    line_params_one(m, idx, cutoff);
     if (zero_acc) {
         const bool first = (idx % m.T) == 0;
         if (zero_acc == 2) {
@@ -89,11 +89,11 @@ __global__ void line_params_kernel(DevModel m, int zero_acc)
     }
 }
 
-loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc)
+loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc, double cutoff)
 {
     const long long n = (long long)m.T * m.n_cells;
     const int bs = fp64_block(n);
-    line_params_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(m, zero_acc);
+    line_params_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(m, zero_acc, cutoff);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }
@@ -116,17 +116,20 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
             const double A = m.line_A[t];
             const long long o = c * m.T + t;
             double J, beta;
-            if (nrm > 0.0) {
+            if (m.trunc && line_off(m.ks[o])) {              // line off in this cell
+                J = m.nbg64[t];
+                beta = 1.0;
+            } else if (nrm > 0.0) {
                 double sj, ej;
                 if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
                 else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
                 J = sj / nrm;
                 beta = ej / nrm;
+                if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
             } else {
                 J = m.nbg64[t];
                 beta = 1.0;
             }
-            if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
             const double rd = A * (beta + J);
             const double ru = (m.g[u] / m.g[l]) * A * J;
             M[l][u] += rd; M[l][l] -= ru;

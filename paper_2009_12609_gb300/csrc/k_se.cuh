@@ -10,7 +10,16 @@ namespace loc {
 
 constexpr int kSeWarps = 4;   // warps per block of the segment-per-cell solve
 
-__device__ __forceinline__ void line_params_one(const DevModel &m, long long idx)
+// {K, S} of a line switched off in this cell by the truncation below
+__device__ __forceinline__ bool line_off(float2 ks)
+{
+    return __float_as_uint(ks.x) == 0x80000000u;
+}
+
+// cutoff > 0: a line whose two levels both hold less than cutoff of the
+// molecules in this cell is marked off there: {K, S} = {-0, 0} (an ordinary
+// line never has K = -0)
+__device__ __forceinline__ void line_params_one(const DevModel &m, long long idx, double cutoff = 0.0)
 {
     const long long c = idx / m.T;                 // layout [cell][line]
     const int t = (int)(idx - c * m.T);
@@ -20,12 +29,16 @@ __device__ __forceinline__ void line_params_one(const DevModel &m, long long idx
     const double xl = m.x[c * m.L + l], xu = m.x[c * m.L + u];
     const double diff = gu * xl - gl * xu;
     float2 ks;
-    if (fabs(diff) <= 1e-30 * gu * xl || (xl == 0.0 && xu == 0.0)) {
+    if (cutoff > 0.0 && xl < cutoff && xu < cutoff) {
+        ks = make_float2(-0.f, 0.f);                            // line off in this cell
+    } else if (fabs(diff) <= 1e-30 * gu * xl || (xl == 0.0 && xu == 0.0)) {
         ks = make_float2(0.f, 0.f);
     } else {
         const double pre = kC * kC * kC * m.line_A[t] / (8.0 * kPI * nu * nu * nu * m.dv);
         const double K = pre * m.n_h2[c] * m.abundance[c] * diff / gl;
-        ks = make_float2((float)K, (float)(gl * xu / diff));
+        float kf = (float)K;
+        if (kf == 0.f) kf = 0.f;                    // an underflow to -0 is not the mark
+        ks = make_float2(kf, (float)(gl * xu / diff));
         if (K < 0.0) atomicAdd(m.maser_count, 1ull);
     }
     m.ks[idx] = ks;
@@ -90,17 +103,20 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
             const double A = m.line_A[t];
             const long long o = c * m.T + t;
             double J, beta;
-            if (nrm > 0.0) {
+            if (m.trunc && line_off(m.ks[o])) {              // line off in this cell
+                J = m.nbg64[t];
+                beta = 1.0;
+            } else if (nrm > 0.0) {
                 double sj, ej;
                 if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
                 else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
                 J = sj * inv_nrm;
                 beta = ej * inv_nrm;
+                if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
             } else {
                 J = m.nbg64[t];
                 beta = 1.0;
             }
-            if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
             M[l * W + u] += A * (beta + J);                     // u -> l
             M[u * W + l] += (m.g[u] / m.g[l]) * A * J;          // l -> u
         }

@@ -475,6 +475,7 @@ static loc_status check_opts(const loc_iter_opts *o)
     CHECK(o->lines_per_pass >= 0, "lines_per_pass must be >= 0");
     CHECK(o->window_sigmas >= 0.0 && std::isfinite(o->window_sigmas), "window_sigmas must be >= 0");
     CHECK(o->profile == 0 || o->profile == 1, "profile must be 0 or 1");
+    CHECK(o->level_cutoff >= 0.0 && o->level_cutoff <= 1e-6, "level_cutoff must be in [0, 1e-6]");
     return LOC_OK;
 }
 
@@ -721,6 +722,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     TRY(check_opts(o));
     if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
     DevModel &D = m->d;
+    D.trunc = o->level_cutoff > 0.0 ? 1 : 0;
     const bool prof = o->profile == 1;
     std::vector<cudaEvent_t> ev;              // 4 per iteration when profiling
     auto mark = [&](size_t idx) -> cudaError_t {
@@ -750,7 +752,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         const size_t b = 4 * (size_t)it;
         if (mark(b) != cudaSuccess) { st = LOC_ECUDA; break; }
         nvtxRangePushA("line parameters");
-        st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1);
+        st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1, o->level_cutoff);
         nvtxRangePop();
         if (st != LOC_OK) break;
         if (mark(b + 1) != cudaSuccess) { st = LOC_ECUDA; break; }
@@ -780,6 +782,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         }
     }
     nvtxRangePop();
+    D.trunc = 0;
     if (st == LOC_ECUDA && g_err[0] == 0) set_error("CUDA error in the iteration: %s", cudaGetErrorString(cudaGetLastError()));
     cudaEventRecord(e1, m->st);
     cudaError_t ce = cudaEventSynchronize(e1);

@@ -63,6 +63,7 @@ struct DevModel {
     // 1D geometry
     int K, n_rays;
     double ray_power;                   // impact parameters R ((j + 1/2) / n_rays)^ray_power (<= 0: 1)
+    int trunc;                          // per-cell line truncation on (lines marked off by line_params)
     long long n_segs;
     double *radius;                     // [K]
     float *v1d;                         // [K] radial velocity
@@ -162,7 +163,7 @@ inline bool distinct_level_pairs(const int32_t *u, const int32_t *l, int n, int 
 // kernel launchers (one per translation unit)
 loc_status launch_geom1d(const DevModel &m, cudaStream_t st);
 loc_status launch_geom1d_scratch(const DevModel &m, cudaStream_t st, int *tan, double *W);
-loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc = 0);
+loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc = 0, double cutoff = 0.0);
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st);

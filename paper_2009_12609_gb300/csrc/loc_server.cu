@@ -56,6 +56,7 @@ struct Request {
     int L = 0, T = 0, P = 0;
     double mass = 0;
     int max_iter = 1, ali = 1;
+    double cutoff = 0.0;
     float tol = 0.f;
     ArenaLayout lay{};
     std::vector<unsigned char> staged;   // inputs in arena order
@@ -271,6 +272,7 @@ static bool admit(loc_server *s, int si, Request *q)
     m.K = q->K;
     m.n_rays = q->n_rays;
     m.ray_power = q->ray_power;
+    m.trunc = q->cutoff > 0.0 ? 1 : 0;
     m.radius = (double *)(b + a.radius);
     m.v1d = (float *)(b + a.v1d);
     m.ray_off = (int *)(b + a.ray_off);
@@ -318,6 +320,7 @@ static bool admit(loc_server *s, int si, Request *q)
     bs.per = per;
     bs.n_groups = (q->T + per - 1) / per;
     bs.inv_dv = (float)(1.0 / q->dv);
+    bs.cutoff = q->cutoff;
     if (cudaMemcpyAsync(s->slots_d + si, &bs, sizeof(bs), cudaMemcpyHostToDevice, s->st) != cudaSuccess)
         return false;
     if (cudaStreamSynchronize(s->st) != cudaSuccess) return false;    // bs leaves scope
@@ -551,7 +554,10 @@ loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_m
         set_error("molecule: two lines or two collision entries join the same pair of levels");
         return LOC_EINVAL;
     }
-    if (o->max_iter < 1 || !(o->tol_tex >= 0.0)) { set_error("options: max_iter >= 1, tol_tex >= 0"); return LOC_EINVAL; }
+    if (o->max_iter < 1 || !(o->tol_tex >= 0.0) || !(o->level_cutoff >= 0.0 && o->level_cutoff <= 1e-6)) {
+        set_error("options: max_iter >= 1, tol_tex >= 0, level_cutoff in [0, 1e-6]");
+        return LOC_EINVAL;
+    }
     Request *q = new (std::nothrow) Request();
     if (!q) { set_error("host allocation failed"); return LOC_ENOMEM; }
     q->K = K;
@@ -566,6 +572,7 @@ loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_m
     q->P = P;
     q->mass = mol->mass_amu;
     q->max_iter = o->max_iter;
+    q->cutoff = o->level_cutoff;
     q->tol = (float)o->tol_tex;
     q->ali = o->ali;
     q->lay = layout_for(*q);

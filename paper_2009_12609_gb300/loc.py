@@ -70,7 +70,8 @@ class loc_iter_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_tex", ctypes.c_double),
                 ("ali", ctypes.c_int), ("precision", ctypes.c_int),
                 ("lines_per_pass", ctypes.c_int), ("window_sigmas", ctypes.c_double),
-                ("profile", ctypes.c_int), ("steps_per_chunk", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("steps_per_chunk", ctypes.c_int),
+                ("level_cutoff", ctypes.c_double)]
 
 
 class loc_iter_report(ctypes.Structure):
@@ -288,11 +289,11 @@ def molecule_desc(mol, keep, n_levels=None):
 
 
 def iter_opts(max_iter=1, tol_tex=0.0, ali=True, precision="fp32", lines_per_pass=0,
-              window_sigmas=0.0, profile=False, steps_per_chunk=0):
+              window_sigmas=0.0, profile=False, steps_per_chunk=0, level_cutoff=0.0):
     prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC}[precision]
     return loc_iter_opts(int(max_iter), float(tol_tex), int(bool(ali)), prec,
                          int(lines_per_pass), float(window_sigmas), int(bool(profile)),
-                         int(steps_per_chunk))
+                         int(steps_per_chunk), float(level_cutoff))
 
 
 # --------------------------------------------------------------------------

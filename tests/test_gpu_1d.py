@@ -261,3 +261,31 @@ def test_power_law_rays_match_oracle(loc, oracle, ray_power, steps_per_chunk):
     bad["ray_power"] = -1.0
     with pytest.raises(loc.LocError):
         loc.Model(bad, mol)
+
+
+def test_level_cutoff_truncates_lines_within_tolerance(loc, oracle):
+    """Per-cell line truncation (the paper's suggested optimisation, Sect. 5):
+    lines whose two levels are empty in a cell are left out there.  The
+    solution still matches the untruncated FP64 oracle, the ray simulation
+    computes fewer updates (line groups of 4, so that whole groups fall
+    below the cutoff in the cold inner cells), and the spectra (which never
+    truncate) agree."""
+    mol = LI.rotor_molecule(n_levels=20)
+    model = LI.cloud1d_rotor(K=64, n_ch=128)
+    n_iter = 20
+    kw = dict(max_iter=n_iter, window_sigmas=8.0, profile=True, lines_per_pass=4)
+    with loc.Model(model, mol) as m:
+        full = m.iterate(**kw)
+        m.reset()
+        cut = m.iterate(level_cutoff=1e-8, **kw)
+        x_ref, _ = oracle.iterate_1d(mol, model, n_iter)
+        assert _tex_err(mol, x_ref, m, oracle) < 1e-4
+        R = model["radius"][-1]
+        p = np.array([0.0, 0.3 * R, 0.8 * R])
+        T = m.spectra(0, p)
+        with pytest.raises(loc.LocError):
+            m.iterate(max_iter=1, level_cutoff=1e-3)
+    assert cut["computed_updates"] < 0.9 * full["computed_updates"]
+    Tref = oracle.spectra_1d(mol, model, x_ref, 0, p)
+    peak = np.abs(Tref).max(axis=1, keepdims=True)
+    assert np.max(np.abs(T - Tref) / peak) < 1e-4

@@ -63,6 +63,30 @@ def test_batch_matches_single_model_path(loc, oracle):
         assert np.max(np.abs(tg[sel] / tr[sel] - 1.0)) < 1e-4
 
 
+def test_batch_level_cutoff_matches_single_model_path(loc, oracle):
+    """Per-cell line truncation in the batched server equals the single-model
+    path with the same cutoff, and stays within tolerance of the oracle."""
+    reqs = _requests(6, seed=404)
+    n_iter, window, cut = 10, 8.0, 1e-8
+    with loc.Server(max_slots=8, iters_per_launch=2, window_sigmas=window) as srv:
+        tickets = [srv.submit(r["model"], LI.rotor_molecule(n_levels=r["n_levels"]),
+                              max_iter=n_iter, level_cutoff=cut) for r in reqs]
+        results = [srv.poll(t, timeout_ms=120000) for t in tickets]
+    for r, (res, x) in zip(reqs, results):
+        assert res["status"] == 0
+        mol = LI.rotor_molecule(n_levels=r["n_levels"])
+        with loc.Model(r["model"], mol) as m:
+            m.iterate(max_iter=n_iter, window_sigmas=window, level_cutoff=cut)
+            xs = m.populations()
+        np.testing.assert_allclose(x, xs, rtol=2e-5, atol=1e-14)
+    r, (res, x) = reqs[0], results[0]
+    mol = LI.rotor_molecule(n_levels=r["n_levels"])
+    xr, _ = oracle.iterate_1d(mol, r["model"], n_iter)
+    tg, tr = oracle.tex(mol, x), oracle.tex(mol, xr)
+    sel = xr[:, mol["line_u"][:tr.shape[0]]].T >= 1e-6
+    assert np.max(np.abs(tg[sel] / tr[sel] - 1.0)) < 1e-4
+
+
 def test_alone_equals_in_mix(loc):
     reqs = _requests(8, seed=202)
     target = reqs[3]
