@@ -97,6 +97,12 @@ def workload(name, n_root=128):
         return dict(name="1D rotor cloud: 256 shells, 12 levels (11 lines), 256 channels, "
                          "50 ALI iterations + spectra",
                     key="rotor1d", mol=mol, model=model, n_iter=50, spectra=True)
+    if name == "hotcore1d":
+        mol = LI.rotor_molecule(n_levels=32)
+        model = LI.cloud1d_rotor(t_core=150.0)
+        return dict(name="1D rotor cloud with a heated centre (T_kin + 150 K exp(-(r/0.15R)^2)): "
+                         "256 shells, 32 levels (31 lines), 256 channels, 50 ALI iterations + spectra",
+                    key="hotcore1d", mol=mol, model=model, n_iter=50, spectra=True)
     if name == "twolevel1d":
         mol = LI.two_level_molecule()
         model = LI.cloud1d_two_level()
@@ -319,7 +325,7 @@ def run_gpu(args, wl):
     R = model["radius"][-1] if is1d else None
     p_spec = np.concatenate([[0.0], (np.arange(model["n_rays"]) + 0.5) * R / model["n_rays"]]) if is1d else None
     opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW, level_cutoff=args.level_cutoff)
-    tune_opts = dict(window_sigmas=WINDOW)
+    tune_opts = dict(window_sigmas=WINDOW, level_cutoff=args.level_cutoff)
 
     m = loc.Model(model, mol)
     stream = torch.cuda.current_stream()
@@ -564,7 +570,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rotor1d",
-                    choices=["rotor1d", "twolevel1d", "grid3d", "octree", "serve"])
+                    choices=["rotor1d", "hotcore1d", "twolevel1d", "grid3d", "octree", "serve"])
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the stream")
     ap.add_argument("--open-requests", type=int, default=256, help="serve: open-loop requests")
     ap.add_argument("--baseline-requests", type=int, default=256,

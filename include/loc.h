@@ -247,7 +247,8 @@ loc_status loc_march(loc_model *m, const loc_iter_opts *o);
  * by timing one ray simulation per candidate with CUDA events on the
  * model's stream; the fastest is used by later calls whose lines_per_pass
  * (steps_per_chunk) is 0.  Runs ray simulations with the current
- * populations (overwrites the accumulators).  best_per, best_chunk (-1:
+ * populations and o->level_cutoff (overwrites the accumulators and the line
+ * parameters).  best_per, best_chunk (-1:
  * whole rays) and best_ms (each may be NULL) receive the choice and its
  * time. */
 loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int *best_chunk,

@@ -63,11 +63,13 @@ def cloud1d_two_level(K=32, n_ch=64, n_rays=None, radius_pc=0.1,
 def cloud1d_rotor(K=256, n_ch=256, seed=SEED_BASE + 1, radius_pc=0.1,
                   abundance=1.0e-5, sigma_ln=0.3, mass_amu=28.0,
                   density_scale=1.0, infall_scale=1.0, t_scale=1.0,
-                  r_clamp_frac=0.0, n_rays=None):
+                  r_clamp_frac=0.0, n_rays=None, t_core=0.0, r_core_frac=0.15):
     """1D core for the multilevel rotor: power-law density perturbed by a
     seeded lognormal factor exp(sigma_ln g - sigma_ln^2/2), g ~ N(0,1) per
     shell, T_kin = 10 + 20 r/R K, the same infall law as the two-level core,
-    band half-width max(2, max|v| + 6 sigma_max) km/s."""
+    band half-width max(2, max|v| + 6 sigma_max) km/s.  t_core > 0 adds a
+    heated centre (an embedded source): T_kin + t_core exp(-(r / r_core)^2)
+    with r_core = r_core_frac R."""
     rng = _rng(seed)
     R = radius_pc * PC
     k = np.arange(K, dtype=np.float64)
@@ -78,6 +80,8 @@ def cloud1d_rotor(K=256, n_ch=256, seed=SEED_BASE + 1, radius_pc=0.1,
     n_h2 = density_scale * np.minimum(1.0e6, 1.0e5 * (r_eval / (0.005 * PC)) ** -1.5)
     n_h2 = n_h2 * np.exp(sigma_ln * g - 0.5 * sigma_ln ** 2)
     t_kin = t_scale * (10.0 + 20.0 * r_mid / R)
+    if t_core > 0.0:
+        t_kin = t_kin + t_core * np.exp(-(r_mid / (r_core_frac * R)) ** 2)
     v = infall_scale * -0.3 * (r_eval / R) ** -0.5 * KMS
     sig_max = _thermal_sigma_max(t_kin.max(), 0.2, mass_amu)
     half = max(2.0, np.abs(v).max() / KMS + 6.0 * sig_max)

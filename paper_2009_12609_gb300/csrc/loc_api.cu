@@ -665,7 +665,9 @@ loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int
         for (int len : {128, 64, 32, 16, 8})
             if (len < longest) runs.push_back(len);
     }
-    TRY(launch_line_params(m->d, m->st));
+    // timed with the per-cell line truncation the iterations will use
+    TRY(launch_line_params(m->d, m->st, 0, o->level_cutoff));
+    m->d.trunc = o->level_cutoff > 0.0 ? 1 : 0;
     cudaEvent_t e0, e1;
     LOC_CUDA_TRY(cudaEventCreate(&e0));
     LOC_CUDA_TRY(cudaEventCreate(&e1));
@@ -696,6 +698,7 @@ loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    m->d.trunc = 0;
     if (st != LOC_OK) return st;
     m->tuned_per = best;
     m->tuned_chunk = best_run;
