@@ -1,14 +1,16 @@
 """1D versus 3D self-consistency (the pattern of the paper's comparison of
 its 1D and 3D codes on one spherical cloud, Sect. 3.2, without hyperfine
-structure): the same Gaussian core with slow infall is solved on 1D shells
-and on a regular 3D grid, and the excitation temperatures (by radius) and
-the emergent central spectrum agree within the 5 % the paper reports
-between its geometries.
+structure): the same Gaussian core with slow infall is solved on 1D shells,
+on a regular 3D grid and on an octree, and the excitation temperatures (by
+radius) and the emergent central spectrum agree within the 5 % the paper
+reports between its geometries.
 
 The 3D box is four cloud radii wide and empty outside the sphere, so every
 line of sight of the periodic grid meets the cloud (or one periodic image
-of it) at most once, as in the 1D model.  Both sides run on the GPU; the
-grid uses the 48 HEALPix directions, the map a direction along +z.
+of it) at most once, as in the 1D model.  All sides run on the GPU; the 3D
+models use the 48 HEALPix directions, the maps a direction along +z.  The
+octree has a 24^3 root refined twice over the sphere, so its leaves there
+match the 96^3 grid's cells.
 """
 import numpy as np
 import pytest
@@ -105,5 +107,82 @@ def test_1d_and_3d_agree_on_a_spherical_core(loc):
     spec3 = T[N // 2, N // 2]
     peak1, peak3 = np.abs(spec1).max(), np.abs(spec3).max()
     assert peak1 > 0.02, peak1                 # a clearly detected line (K)
+    assert abs(peak3 / peak1 - 1.0) < 0.05, (peak1, peak3)
+    assert np.abs(spec3 - spec1).max() < 0.08 * peak1, np.abs(spec3 - spec1).max() / peak1
+
+
+def _octree_sphere(N0=24, levels=2, dirs=None):
+    """Level-ordered octree of the same core: level-0 cells in raster order
+    (x fastest), then the 8 children (octant cx + 2 cy + 4 cz) of every
+    refined cell of the previous level in the order of their parents; a cell
+    is refined when it reaches into the sphere (centre within R + half its
+    diagonal) above the deepest level.  Every cell holds the analytic fields
+    at its centre."""
+    L = 4.0 * R
+    h0 = L / N0
+    c = (np.arange(N0) + 0.5) * h0 - 0.5 * L
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    cen = np.stack([a.transpose(2, 1, 0).reshape(-1) for a in (X, Y, Z)], axis=1)
+    centres, refine, lev = [cen], [], []
+    for lv in range(levels + 1):
+        h = h0 / 2 ** lv
+        r = np.sqrt((centres[lv] ** 2).sum(axis=1))
+        ref = (r < R + 0.5 * np.sqrt(3.0) * h) if lv < levels else np.zeros(len(r), bool)
+        refine.append(ref.astype(np.int32))
+        lev.append(np.full(len(r), lv))
+        if lv == levels:
+            break
+        par = centres[lv][ref]
+        off = np.array([[(o & 1) - 0.5, ((o >> 1) & 1) - 0.5, ((o >> 2) & 1) - 0.5]
+                        for o in range(8)]) * (0.5 * h)
+        centres.append((par[:, None, :] + off[None, :, :]).reshape(-1, 3))
+    P = np.concatenate(centres)
+    r = np.sqrt((P ** 2).sum(axis=1))
+    vr = _v(r)
+    rr = np.maximum(r, 1e-30)
+    M = len(P)
+    model = dict(geometry="octree3d", n_root=N0, h0=h0, levels=levels,
+                 refine=np.concatenate(refine), n_h2=_n(r), t_kin=np.full(M, 15.0),
+                 sigma_turb=np.full(M, 0.2 * KMS), abundance=np.full(M, 3e-9),
+                 vx=vr * P[:, 0] / rr, vy=vr * P[:, 1] / rr, vz=vr * P[:, 2] / rr,
+                 dirs=LI.healpix_ring_directions(2) if dirs is None else dirs,
+                 n_ch=N_CH, v_min=-HALF * KMS, dv=2 * HALF * KMS / N_CH, t_bg=2.73)
+    return model, r, np.concatenate(refine) == 0
+
+
+def test_1d_and_octree_agree_on_a_spherical_core(loc):
+    mol = LI.rotor_molecule(n_levels=5)
+    m1 = _cloud_1d()
+    mo, ro, leaf = _octree_sphere()
+    n_iter = 25
+    with loc.Model(m1, mol) as a:
+        a.iterate(max_iter=n_iter, window_sigmas=8.0)
+        tex1 = [a.tex(t) for t in range(2)]
+        K = len(m1["radius"])
+        h_fine = mo["h0"] / 2 ** mo["levels"]
+        spec1 = a.spectra(0, [h_fine / np.sqrt(2.0)])[0]
+    with loc.Model(mo, mol) as b:
+        b.iterate(max_iter=n_iter, window_sigmas=8.0)
+        xo = b.populations()
+        texo = [b.tex(t) for t in range(2)]
+    r_mid = (np.arange(K) + 0.5) * R / K
+    rl = ro[leaf]                       # results are per leaf, in cell order
+    inside = rl < 0.9 * R
+    assert inside.sum() > 10000
+    for t in range(2):
+        ref = np.interp(rl[inside], r_mid, tex1[t])
+        rel = np.abs(texo[t][inside] / ref - 1.0)
+        assert np.median(rel) < 0.02, (t, np.median(rel))
+        assert np.percentile(rel, 95) < 0.05, (t, np.percentile(rel, 95))
+    # central pixel of the finest-level map along +z against the 1D spectrum
+    moz, _, _ = _octree_sphere(dirs=np.array([[0.0, 0.0, 1.0]]))
+    with loc.Model(moz, mol) as c:
+        c.set_populations(xo)
+        lv = moz["levels"]
+        Mpix = moz["n_root"] << lv
+        T = c.map3d(0, 0, level=lv).reshape(Mpix, Mpix, -1)
+    spec3 = T[Mpix // 2, Mpix // 2]
+    peak1, peak3 = np.abs(spec1).max(), np.abs(spec3).max()
+    assert peak1 > 0.02, peak1
     assert abs(peak3 / peak1 - 1.0) < 0.05, (peak1, peak3)
     assert np.abs(spec3 - spec1).max() < 0.08 * peak1, np.abs(spec3 - spec1).max() / peak1
