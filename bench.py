@@ -436,11 +436,12 @@ def run_gpu(args, wl):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
     e2e_val = replicas_throughput(upd_step, world, e2e_s)
 
-    # per iteration: line parameters, march (1D runs: affine, scan, run),
-    # equilibrium; per step: the LTE reset, and for spectra line parameters,
-    # step geometry and the spectrum kernel
-    per_iter_launches = 5 if runs else 3
-    gpu_launches = args.steps * (iters * per_iter_launches + (4 if wl["spectra"] else 1))
+    # per iteration: march (1D runs: affine, scan, run) and equilibrium; the
+    # line parameters once per call (the solve prepares every later
+    # iteration's); per step also the LTE reset, and for spectra line
+    # parameters, step geometry and the spectrum kernel
+    per_iter_launches = 4 if runs else 2
+    gpu_launches = args.steps * (iters * per_iter_launches + 1 + (4 if wl["spectra"] else 1))
 
     if rank == 0:
         cpu = None

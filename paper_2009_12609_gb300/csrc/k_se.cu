@@ -101,7 +101,8 @@ loc_status launch_line_params(const DevModel &m, cudaStream_t st, int zero_acc, 
 // One thread per cell (large models: enough cells to fill the GPU, FP64
 // throughput is the limit).  Same rate assembly order as the warp version.
 template <int LMAX>
-__global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int fp64_acc, int want_dtex)
+__global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int fp64_acc, int want_dtex,
+                                                        int next, double cutoff)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float my_d = 0.f;
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
             const double b = tex_of(m, t, xs);
             my_d = fmaxf(my_d, (float)(fabs(b - a) / fabs(a)));
         }
+        for (int t = 0; next && t < m.T; t++) next_line_params(m, c, t, xs, fp64_acc, cutoff, t == 0);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) my_d = fmaxf(my_d, __shfl_xor_sync(0xffffffffu, my_d, off));
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
 constexpr long long kSeThreadCells = 1ll << 16;
 
 template <int LMAX>
-__global__ void __launch_bounds__(kSeWarps * 32) se_kernel(DevModel m, int ali, int fp64_acc, int want_dtex)
+__global__ void __launch_bounds__(kSeWarps * 32) se_kernel(DevModel m, int ali, int fp64_acc, int want_dtex,
+                                                            int next, double cutoff)
 {
     constexpr int LW = LMAX;                        // lanes per cell
     constexpr int CPW = 32 / LW;                    // cells per warp
@@ -202,18 +205,20 @@ __global__ void __launch_bounds__(kSeWarps * 32) se_kernel(DevModel m, int ali, 
     long long c = c0 + seg;
     const bool valid = c < m.n_cells;
     if (!valid) c = m.n_cells - 1;                  // repeat a real cell, store nothing
-    float my_d = se_seg_cell<LMAX, LW>(m, c, valid, ali, fp64_acc, sl, M, M + LMAX * W, want_dtex != 0);
+    float my_d = se_seg_cell<LMAX, LW>(m, c, valid, ali, fp64_acc, sl, M, M + LMAX * W, want_dtex != 0,
+                                       next != 0, cutoff);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) my_d = fmaxf(my_d, __shfl_xor_sync(0xffffffffu, my_d, off));
     if (lane == 0 && my_d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(my_d));
 }
 
 template <int LMAX>
-static loc_status launch_se_l(const DevModel &m, int ali, int fp64_acc, int want_dtex, cudaStream_t st)
+static loc_status launch_se_l(const DevModel &m, int ali, int fp64_acc, int want_dtex, int next,
+                              double cutoff, cudaStream_t st)
 {
     if (m.n_cells >= kSeThreadCells) {
         const unsigned nbt = (unsigned)((m.n_cells + 127) / 128);
-        se_thread_kernel<LMAX><<<nbt, 128, 0, st>>>(m, ali, fp64_acc, want_dtex);
+        se_thread_kernel<LMAX><<<nbt, 128, 0, st>>>(m, ali, fp64_acc, want_dtex, next, cutoff);
         LOC_CUDA_TRY(cudaGetLastError());
         return LOC_OK;
     }
@@ -232,17 +237,18 @@ static loc_status launch_se_l(const DevModel &m, int ali, int fp64_acc, int want
     LOC_CUDA_TRY(cudaFuncSetAttribute(se_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long cells_per_block = (long long)wpb * CPW;
     const unsigned nb = (unsigned)((m.n_cells + cells_per_block - 1) / cells_per_block);
-    se_kernel<LMAX><<<nb, wpb * 32, smem, st>>>(m, ali, fp64_acc, want_dtex);
+    se_kernel<LMAX><<<nb, wpb * 32, smem, st>>>(m, ali, fp64_acc, want_dtex, next, cutoff);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }
 
-loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st, int want_dtex)
+loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st, int want_dtex, int next,
+                     double cutoff)
 {
-    if (m.L <= 4) return launch_se_l<4>(m, ali, fp64_acc, want_dtex, st);
-    if (m.L <= 8) return launch_se_l<8>(m, ali, fp64_acc, want_dtex, st);
-    if (m.L <= 16) return launch_se_l<16>(m, ali, fp64_acc, want_dtex, st);
-    return launch_se_l<32>(m, ali, fp64_acc, want_dtex, st);
+    if (m.L <= 4) return launch_se_l<4>(m, ali, fp64_acc, want_dtex, next, cutoff, st);
+    if (m.L <= 8) return launch_se_l<8>(m, ali, fp64_acc, want_dtex, next, cutoff, st);
+    if (m.L <= 16) return launch_se_l<16>(m, ali, fp64_acc, want_dtex, next, cutoff, st);
+    return launch_se_l<32>(m, ali, fp64_acc, want_dtex, next, cutoff, st);
 }
 
 // Collision rate table of the model (n_H2 and T_kin are fixed): one thread

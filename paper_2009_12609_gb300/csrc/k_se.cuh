@@ -19,14 +19,13 @@ __device__ __forceinline__ bool line_off(float2 ks)
 // cutoff > 0: a line whose two levels both hold less than cutoff of the
 // molecules in this cell is marked off there: {K, S} = {-0, 0} (an ordinary
 // line never has K = -0)
-__device__ __forceinline__ void line_params_one(const DevModel &m, long long idx, double cutoff = 0.0)
+__device__ __forceinline__ void line_params_at(const DevModel &m, long long c, int t, double xl, double xu,
+                                               double cutoff)
 {
-    const long long c = idx / m.T;                 // layout [cell][line]
-    const int t = (int)(idx - c * m.T);
+    const long long idx = c * m.T + t;             // layout [cell][line]
     const int u = m.line_u[t], l = m.line_l[t];
     const double nu = m.line_nu[t];
     const double gu = m.g[u], gl = m.g[l];
-    const double xl = m.x[c * m.L + l], xu = m.x[c * m.L + u];
     const double diff = gu * xl - gl * xu;
     float2 ks;
     if (cutoff > 0.0 && xl < cutoff && xu < cutoff) {
@@ -42,6 +41,33 @@ __device__ __forceinline__ void line_params_one(const DevModel &m, long long idx
         if (K < 0.0) atomicAdd(m.maser_count, 1ull);
     }
     m.ks[idx] = ks;
+}
+
+// entry idx = c T + t from the current populations m.x
+__device__ __forceinline__ void line_params_one(const DevModel &m, long long idx, double cutoff = 0.0)
+{
+    const long long c = idx / m.T;
+    const int t = (int)(idx - c * m.T);
+    line_params_at(m, c, t, m.x[c * m.L + m.line_l[t]], m.x[c * m.L + m.line_u[t]], cutoff);
+}
+
+// The solve of one ALI iteration prepares the next one in the same pass:
+// line t's {K, S} from the cell's new populations xn, and its accumulators
+// cleared (lane `first` also clears NORM) -- what line_params_kernel does at
+// the start of an iteration, without the launch.
+__device__ __forceinline__ void next_line_params(const DevModel &m, long long c, int t, const double *xn,
+                                                 int fp64_acc, double cutoff, bool first)
+{
+    line_params_at(m, c, t, xn[m.line_l[t]], xn[m.line_u[t]], cutoff);
+    const long long o = c * m.T + t;
+    if (fp64_acc) {
+        m.acc64[2 * o] = 0.0;
+        m.acc64[2 * o + 1] = 0.0;
+        if (first) m.norm64[c] = 0.0;
+    } else {
+        m.acc[o] = make_float2(0.f, 0.f);
+        if (first) m.norm[c] = 0.f;
+    }
 }
 
 __device__ __forceinline__ double tex_of(const DevModel &m, int t, const double *x)
@@ -85,10 +111,12 @@ __device__ __forceinline__ double2 coll_rate(const DevModel &m, long long c, int
 // first, then collisions, then the diagonal as column sums -- a fixed order.
 // Elimination with partial pivoting runs with lanes over columns; back
 // substitution with lanes over rows, one broadcast per unknown.
+// next: also prepare the next iteration (next_line_params) with `cutoff`.
 template <int LMAX, int LW>
 __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, bool valid, int ali,
                                              int fp64_acc, int sl, double *M, double *F,
-                                             bool want_dtex = true)
+                                             bool want_dtex = true, bool next = false,
+                                             double cutoff = 0.0)
 {
     constexpr int W = LMAX + 2;
     const int L = m.L;
@@ -195,6 +223,8 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
             my_d = fmaxf(my_d, (float)(fabs(b - a) / fabs(a)));
         }
     }
+    if (valid && next)
+        for (int t = sl; t < m.T; t += LW) next_line_params(m, c, t, F, fp64_acc, cutoff, t == 0);
     __syncwarp();
     return my_d;
 }

@@ -747,6 +747,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     int it = 0;
     float dtex = 0.f;
     bool converged = false;
+    const bool fuse = !(o->tol_tex > 0.0);
     loc_status st = LOC_OK;
     // NVTX ranges mark the host-side phases of every iteration for timeline
     // tools (no cost without an attached tool)
@@ -754,10 +755,17 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     for (it = 0; it < o->max_iter; it++) {
         const size_t b = 4 * (size_t)it;
         if (mark(b) != cudaSuccess) { st = LOC_ECUDA; break; }
-        nvtxRangePushA("line parameters");
-        st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1, o->level_cutoff);
-        nvtxRangePop();
-        if (st != LOC_OK) break;
+        // with a fixed iteration count (no tolerance) the first iteration's
+        // line parameters (and cleared accumulators) come from their own
+        // launch and every later iteration's from the previous iteration's
+        // solve; with a tolerance, a converged call must leave the last ray
+        // simulation's accumulators readable, so every iteration launches them
+        if (it == 0 || !fuse) {
+            nvtxRangePushA("line parameters");
+            st = launch_line_params(D, m->st, o->precision == LOC_FP64_ACC ? 2 : 1, o->level_cutoff);
+            nvtxRangePop();
+            if (st != LOC_OK) break;
+        }
         if (mark(b + 1) != cudaSuccess) { st = LOC_ECUDA; break; }
         nvtxRangePushA("ray march");
         st = march_impl(m, o, true);
@@ -766,8 +774,12 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         if (mark(b + 2) != cudaSuccess) { st = LOC_ECUDA; break; }
         // the metric is read when a tolerance is set, and after the last iteration
         const int want = (o->tol_tex > 0.0 || it == o->max_iter - 1) ? 1 : 0;
+        if (want && it > 0 && fuse) {
+            if (cudaMemsetAsync(D.dtex_bits, 0, sizeof(unsigned), m->st) != cudaSuccess) { st = LOC_ECUDA; break; }
+        }
+        const int next = (fuse && it < o->max_iter - 1) ? 1 : 0;
         nvtxRangePushA("statistical equilibrium");
-        st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st, want);
+        st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st, want, next, o->level_cutoff);
         nvtxRangePop();
         if (st != LOC_OK) break;
         if (mark(b + 3) != cudaSuccess) { st = LOC_ECUDA; break; }

@@ -170,7 +170,10 @@ loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStr
 loc_status launch_march1d_ranges(const DevModel &m, const MarchArgs &a, int *max_w_dev, cudaStream_t st);
 loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 // want_dtex = 0: skip the convergence metric (nothing reads it this iteration)
-loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st, int want_dtex = 1);
+// next = 1: the solve also computes the next iteration's line parameters
+// from the new populations (with cutoff) and clears its accumulators
+loc_status launch_se(const DevModel &m, int ali, int fp64_acc, cudaStream_t st, int want_dtex = 1,
+                     int next = 0, double cutoff = 0.0);
 loc_status launch_lte(const DevModel &m, cudaStream_t st);
 loc_status launch_coll_rates(const DevModel &m, double2 *out, cudaStream_t st);
 loc_status launch_bg(const DevModel &m, cudaStream_t st);
