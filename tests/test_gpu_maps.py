@@ -63,6 +63,26 @@ def test_octree_maps_match_oracle(loc, oracle):
                 _check(T, oracle.map_3d(mol, model, x, 1, model["dirs"][d], lam=lam))
 
 
+def test_lte_maps_match_oracle(loc, oracle):
+    """The LTE variant of the maps (the paper contrasts LTE and non-LTE line
+    emission, Sect. 3.3): populations reset to Boltzmann at T_kin on the
+    device, compared with the oracle's own LTE populations and map."""
+    mol = LI.rotor_molecule(n_levels=5)
+    for model in (LI.small_grid3d(N=6, n_ch=24, nside=1, abundance=3e-6),
+                  LI.small_octree(N=4, levels=2, n_ch=20, nside=1, refine_frac=0.3)):
+        with loc.Model(model, mol) as m:
+            m.iterate(max_iter=2, window_sigmas=8.0)
+            m.reset()
+            x = m.populations()
+            leaf = (model["refine"] == 0) if model["geometry"] == "octree3d" else slice(None)
+            x_lte = oracle.lte_populations(mol, np.asarray(model["t_kin"])[leaf])
+            np.testing.assert_allclose(x, x_lte, rtol=1e-10, atol=1e-300)
+            lam = model.get("levels", 0)
+            for d in (0, 3):
+                _check(m.map3d(0, d, level=lam),
+                       oracle.map_3d(mol, model, x_lte, 0, model["dirs"][d], lam=lam))
+
+
 def test_grid_full_size_sampled(loc, oracle):
     model = LI.grid3d_cloud()
     mol = LI.rotor_molecule()
