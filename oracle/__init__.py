@@ -185,14 +185,33 @@ def march_1d(mol, model, Kp, S, n_levels=None):
     return SIJ, ESC, NORM
 
 
-def se_solve(mol, model, SIJ, ESC, NORM, S, ali=True, n_levels=None):
+def line_off(mol, x, cutoff, n_levels=None):
+    """Per-cell line truncation mask [line][cell] (uint8) for populations x."""
+    lib = _load()
+    M = _Mol(mol, n_levels)
+    x = _f64(x)
+    n = x.shape[0]
+    off = np.zeros((M.T, n), np.uint8)
+    lib.lo_line_off(M.ref, n, _p(x), ctypes.c_double(cutoff),
+                    off.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return off
+
+
+def se_solve(mol, model, SIJ, ESC, NORM, S, ali=True, n_levels=None, off=None):
+    """Equilibrium populations; off: optional [line][cell] truncation mask
+    (those lines take J = n_bg, beta = 1)."""
     lib = _load()
     M = _Mol(mol, n_levels)
     n = len(model["n_h2"])
     x = np.zeros((n, M.L))
-    bad = lib.lo_se_solve(M.ref, n, _p(_f64(model["n_h2"])), _p(_f64(model["t_kin"])),
-                          ctypes.c_double(model["t_bg"]), int(bool(ali)), _p(_f64(SIJ)),
-                          _p(_f64(ESC)), _p(_f64(NORM)), _p(_f64(S)), _p(x))
+    if off is None:
+        offp = None
+    else:
+        off = np.ascontiguousarray(off, dtype=np.uint8)
+        offp = off.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    bad = lib.lo_se_solve_off(M.ref, n, _p(_f64(model["n_h2"])), _p(_f64(model["t_kin"])),
+                              ctypes.c_double(model["t_bg"]), int(bool(ali)), _p(_f64(SIJ)),
+                              _p(_f64(ESC)), _p(_f64(NORM)), _p(_f64(S)), offp, _p(x))
     if bad:
         raise ArithmeticError(f"{bad} singular rate matrices")
     return x
@@ -215,20 +234,21 @@ def max_rel_dtex(mol, x_old, x_new, n_levels=None):
     return lib.lo_max_rel_dtex(M.ref, x_old.shape[0], _p(x_old), _p(_f64(x_new)))
 
 
-def iterate_1d(mol, model, n_iter, ali=True, x0=None, n_levels=None):
-    """Run n_iter ALI iterations from LTE (or x0).  Returns (x, dtex[n_iter])."""
+def iterate_1d(mol, model, n_iter, ali=True, x0=None, n_levels=None, level_cutoff=0.0):
+    """Run n_iter ALI iterations from LTE (or x0), with per-cell line
+    truncation when level_cutoff > 0.  Returns (x, dtex[n_iter])."""
     lib = _load()
     M = _Mol(mol, n_levels)
     K = len(model["radius"])
     x = lte_populations(mol, model["t_kin"], n_levels) if x0 is None else _f64(x0).copy()
     dt = np.zeros(max(1, n_iter))
-    bad = lib.lo_iterate_1d(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["n_h2"])),
-                            _p(_f64(model["t_kin"])), _p(_f64(model["sigma_turb"])),
-                            _p(_f64(model["abundance"])), _p(_f64(model["v"])),
-                            int(model["n_ch"]), ctypes.c_double(model["v_min"]),
-                            ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
-                            ctypes.c_double(model["t_bg"]), int(bool(ali)), int(n_iter),
-                            _p(x), _p(dt))
+    bad = lib.lo_iterate_1d_cut(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["n_h2"])),
+                                _p(_f64(model["t_kin"])), _p(_f64(model["sigma_turb"])),
+                                _p(_f64(model["abundance"])), _p(_f64(model["v"])),
+                                int(model["n_ch"]), ctypes.c_double(model["v_min"]),
+                                ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
+                                ctypes.c_double(model["t_bg"]), int(bool(ali)), int(n_iter),
+                                ctypes.c_double(level_cutoff), _p(x), _p(dt))
     if bad:
         raise ArithmeticError(f"{bad} singular rate matrices")
     return x, dt[:n_iter]

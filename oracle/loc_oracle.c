@@ -20,7 +20,8 @@
  * the reading used is stated next to the code.
  *
  * Parity status: every function here is pinned by tests in tests/ against
- * closed forms, invariants or brute force, except the infall line shape
+ * closed forms, invariants or brute force (the per-cell line truncation by
+ * tests/test_oracle_truncation.py), except the infall line shape
  * (qualitative blue asymmetry only) -- see the test module docstrings.
  */
 #include <math.h>
@@ -374,10 +375,29 @@ static int lo_gauss_solve(int n, double *M, double *b)
     return 0;
 }
 
-int lo_se_solve(const lo_molecule *m, int n_cells, const double *n_h2,
-                const double *t_kin, double t_bg, int ali,
-                const double *SIJ, const double *ESC, const double *NORM,
-                const double *S, double *x_out)
+/* Per-cell line truncation (Sect. 5 proposes computing, cell by cell, only   */
+/* the transitions whose levels are populated, without giving a rule; this   */
+/* is our reading): line t is off in cell c when both of its levels hold     */
+/* less than `cutoff` of the molecules, off[t][c] = 1.  An off line has no   */
+/* opacity in that cell (Kp = 0, S = 0: it neither absorbs nor emits there)  */
+/* and its rates use the background field, J = n_bg with beta = 1.           */
+void lo_line_off(const lo_molecule *m, int n_cells, const double *x, double cutoff,
+                 unsigned char *off)
+{
+    const int L = m->n_levels;
+    for (int t = 0; t < m->n_lines; t++) {
+        const int u = m->line_u[t], l = m->line_l[t];
+        for (int c = 0; c < n_cells; c++)
+            off[(size_t)t * n_cells + c] =
+                (cutoff > 0.0 && x[(size_t)c * L + l] < cutoff && x[(size_t)c * L + u] < cutoff) ? 1 : 0;
+    }
+}
+
+/* off: [line][cell] truncation mask of lo_line_off, or NULL (none). */
+int lo_se_solve_off(const lo_molecule *m, int n_cells, const double *n_h2,
+                    const double *t_kin, double t_bg, int ali,
+                    const double *SIJ, const double *ESC, const double *NORM,
+                    const double *S, const unsigned char *off, double *x_out)
 {
     const int L = m->n_levels, T = m->n_lines;
     int bad = 0;
@@ -391,7 +411,10 @@ int lo_se_solve(const lo_molecule *m, int n_cells, const double *n_h2,
             const double A = m->line_A[t];
             const size_t o = (size_t)t * n_cells + c;
             double J, beta;
-            if (NORM[c] > 0.0) {
+            if (off && off[o]) {
+                J = lo_bg_occupation(m->line_nu[t], t_bg);
+                beta = 1.0;
+            } else if (NORM[c] > 0.0) {
                 J = SIJ[o] / NORM[c];
                 beta = ESC[o] / NORM[c];
             } else {
@@ -426,6 +449,14 @@ int lo_se_solve(const lo_molecule *m, int n_cells, const double *n_h2,
         free(R); free(M); free(b);
     }
     return bad;
+}
+
+int lo_se_solve(const lo_molecule *m, int n_cells, const double *n_h2,
+                const double *t_kin, double t_bg, int ali,
+                const double *SIJ, const double *ESC, const double *NORM,
+                const double *S, double *x_out)
+{
+    return lo_se_solve_off(m, n_cells, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, NULL, x_out);
 }
 
 /* Excitation temperature T_ex = (h nu / k) / ln(g_u x_l / (g_l x_u)),
@@ -469,13 +500,15 @@ double lo_max_rel_dtex(const lo_molecule *m, int n_cells, const double *x_old,
 
 /* The ALI loop for a 1D model (Sect. 2): start from x (LTE or given),
  * then n_iter times: line parameters -> ray simulation -> equilibrium.
- * dtex[it] receives the per-iteration convergence metric. */
-int lo_iterate_1d(const lo_molecule *m, int K, const double *R,
-                  const double *n_h2, const double *t_kin,
-                  const double *sigma_turb, const double *abundance,
-                  const double *v, int n_ch, double v_min, double dv,
-                  int n_rays, double ray_power, double t_bg, int ali, int n_iter,
-                  double *x, double *dtex)
+ * dtex[it] receives the per-iteration convergence metric.  cutoff > 0:
+ * per-cell line truncation (lo_line_off) from each iteration's starting
+ * populations. */
+int lo_iterate_1d_cut(const lo_molecule *m, int K, const double *R,
+                      const double *n_h2, const double *t_kin,
+                      const double *sigma_turb, const double *abundance,
+                      const double *v, int n_ch, double v_min, double dv,
+                      int n_rays, double ray_power, double t_bg, int ali, int n_iter,
+                      double cutoff, double *x, double *dtex)
 {
     const int T = m->n_lines, L = m->n_levels;
     double *Kp = (double *)malloc(sizeof(double) * T * K);
@@ -484,16 +517,31 @@ int lo_iterate_1d(const lo_molecule *m, int K, const double *R,
     double *ESC = (double *)malloc(sizeof(double) * T * K);
     double *NORM = (double *)malloc(sizeof(double) * K);
     double *xn = (double *)malloc(sizeof(double) * L * K);
+    unsigned char *off = (unsigned char *)malloc((size_t)T * K);
     int bad = 0;
     for (int it = 0; it < n_iter; it++) {
         lo_line_params(m, K, n_h2, abundance, dv, x, Kp, S);
+        lo_line_off(m, K, x, cutoff, off);
+        for (size_t o = 0; o < (size_t)T * K; o++)
+            if (off[o]) { Kp[o] = 0.0; S[o] = 0.0; }
         lo_march_1d(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S, SIJ, ESC, NORM);
-        bad += lo_se_solve(m, K, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, xn);
+        bad += lo_se_solve_off(m, K, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, off, xn);
         if (dtex) dtex[it] = lo_max_rel_dtex(m, K, x, xn);
         memcpy(x, xn, sizeof(double) * L * K);
     }
-    free(Kp); free(S); free(SIJ); free(ESC); free(NORM); free(xn);
+    free(Kp); free(S); free(SIJ); free(ESC); free(NORM); free(xn); free(off);
     return bad;
+}
+
+int lo_iterate_1d(const lo_molecule *m, int K, const double *R,
+                  const double *n_h2, const double *t_kin,
+                  const double *sigma_turb, const double *abundance,
+                  const double *v, int n_ch, double v_min, double dv,
+                  int n_rays, double ray_power, double t_bg, int ali, int n_iter,
+                  double *x, double *dtex)
+{
+    return lo_iterate_1d_cut(m, K, R, n_h2, t_kin, sigma_turb, abundance, v, n_ch, v_min, dv,
+                             n_rays, ray_power, t_bg, ali, n_iter, 0.0, x, dtex);
 }
 
 /* Emergent spectra of a 1D model (Sect. 2: final line-of-sight integration

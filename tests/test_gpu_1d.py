@@ -266,10 +266,11 @@ def test_power_law_rays_match_oracle(loc, oracle, ray_power, steps_per_chunk):
 def test_level_cutoff_truncates_lines_within_tolerance(loc, oracle):
     """Per-cell line truncation (the paper's suggested optimisation, Sect. 5):
     lines whose two levels are empty in a cell are left out there.  The
-    solution still matches the untruncated FP64 oracle, the ray simulation
-    computes fewer updates (line groups of 4, so that whole groups fall
-    below the cutoff in the cold inner cells), and the spectra (which never
-    truncate) agree."""
+    populations match the oracle's truncated iteration level by level (down
+    to 1e-20), the monitored excitation temperatures also match the
+    untruncated oracle, the ray simulation computes fewer updates (line
+    groups of 4, so that whole groups fall below the cutoff in the cold
+    inner cells), and the spectra (which never truncate) agree."""
     mol = LI.rotor_molecule(n_levels=20)
     model = LI.cloud1d_rotor(K=64, n_ch=128)
     n_iter = 20
@@ -280,6 +281,11 @@ def test_level_cutoff_truncates_lines_within_tolerance(loc, oracle):
         cut = m.iterate(level_cutoff=1e-8, **kw)
         x_ref, _ = oracle.iterate_1d(mol, model, n_iter)
         assert _tex_err(mol, x_ref, m, oracle) < 1e-4
+        x_cut, _ = oracle.iterate_1d(mol, model, n_iter, level_cutoff=1e-8)
+        assert _tex_err(mol, x_cut, m, oracle) < 1e-4
+        xg = m.populations()
+        sel = x_cut > 1e-20
+        assert np.max(np.abs(xg[sel] / x_cut[sel] - 1.0)) < 1e-3
         R = model["radius"][-1]
         p = np.array([0.0, 0.3 * R, 0.8 * R])
         T = m.spectra(0, p)
