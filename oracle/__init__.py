@@ -320,11 +320,33 @@ def march_grid3d(mol, model, Kp, S, F=FIXED_BITS, dir_range=None, ray_stride=1,
     return SIJ, ESC, NORM
 
 
-def iterate_grid3d(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels=None):
+def _truncated_step(mol, model, x, march, ali, level_cutoff, n_levels):
+    """One ALI iteration with per-cell line truncation (lo_line_off reading):
+    off lines get Kp = S = 0 in the march and J = n_bg, beta = 1 in the solve."""
+    Kp, S = line_params(mol, model, x, n_levels)
+    off = line_off(mol, x, level_cutoff, n_levels)
+    Kp[off == 1] = 0.0
+    S[off == 1] = 0.0
+    SIJ, ESC, NORM = march(Kp, S)
+    return se_solve(mol, model, SIJ, ESC, NORM, S, ali, n_levels, off=off)
+
+
+def iterate_grid3d(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels=None,
+                   level_cutoff=0.0):
+    """n_iter ALI iterations on a regular grid (per-cell line truncation when
+    level_cutoff > 0).  Returns (x, dtex[n_iter])."""
     lib = _load()
     M = _Mol(mol, n_levels)
     N = int(model["n_root"])
     x = lte_populations(mol, model["t_kin"], n_levels) if x0 is None else _f64(x0).copy()
+    if level_cutoff > 0.0:
+        dt = np.zeros(n_iter)
+        for it in range(n_iter):
+            xn = _truncated_step(mol, model, x, lambda K_, S_: march_grid3d(mol, model, K_, S_, F, n_levels=n_levels),
+                                 ali, level_cutoff, n_levels)
+            dt[it] = max_rel_dtex(mol, x, xn, n_levels)
+            x = xn
+        return x, dt
     dt = np.zeros(max(1, n_iter))
     dirs = _f64(model["dirs"])
     bad = lib.lo_iterate_grid3d(M.ref, N, ctypes.c_double(model["h0"]), int(F),
@@ -418,15 +440,21 @@ def leaf_model(model):
     return out
 
 
-def iterate_octree(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels=None):
-    """n_iter ALI iterations on an octree; populations per leaf."""
+def iterate_octree(mol, model, n_iter, ali=True, x0=None, F=FIXED_BITS, n_levels=None,
+                   level_cutoff=0.0):
+    """n_iter ALI iterations on an octree; populations per leaf (per-cell line
+    truncation when level_cutoff > 0)."""
     lm = leaf_model(model)
     x = lte_populations(mol, lm["t_kin"], n_levels) if x0 is None else _f64(x0).copy()
     dt = np.zeros(n_iter)
     for it in range(n_iter):
-        Kp, S = line_params(mol, lm, x, n_levels)
-        SIJ, ESC, NORM = march_octree(mol, model, Kp, S, F, n_levels)
-        xn = se_solve(mol, lm, SIJ, ESC, NORM, S, ali, n_levels)
+        if level_cutoff > 0.0:
+            xn = _truncated_step(mol, lm, x, lambda K_, S_: march_octree(mol, model, K_, S_, F, n_levels),
+                                 ali, level_cutoff, n_levels)
+        else:
+            Kp, S = line_params(mol, lm, x, n_levels)
+            SIJ, ESC, NORM = march_octree(mol, model, Kp, S, F, n_levels)
+            xn = se_solve(mol, lm, SIJ, ESC, NORM, S, ali, n_levels)
         dt[it] = max_rel_dtex(mol, x, xn, n_levels)
         x = xn
     return x, dt

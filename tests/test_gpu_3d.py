@@ -87,6 +87,26 @@ def test_iterations_small(loc, oracle):
                 assert err < 1e-4, (t, err)
 
 
+def test_iterations_with_level_cutoff(loc, oracle):
+    """Per-cell line truncation on a grid: populations level by level (down
+    to 1e-20) and T_ex against the oracle's truncated iteration."""
+    mol = LI.rotor_molecule(n_levels=14)
+    g = LI.small_grid3d(N=8, n_ch=32, nside=2, abundance=3e-4)
+    with loc.Model(g, mol) as m:
+        m.iterate(max_iter=4, window_sigmas=8.0, level_cutoff=1e-8)
+        xg = m.populations()
+        x_ref, _ = oracle.iterate_grid3d(mol, g, 4, level_cutoff=1e-8)
+        assert oracle.line_off(mol, x_ref, 1e-8).mean() > 0.1
+        tref = oracle.tex(mol, x_ref)
+        for t in range(tref.shape[0]):
+            sel = x_ref[:, mol["line_u"][t]] >= 1e-6
+            if sel.any():
+                err = np.max(np.abs(m.tex(t)[sel] / tref[t, sel] - 1.0))
+                assert err < 1e-4, (t, err)
+    sel = x_ref > 1e-20
+    assert np.max(np.abs(xg[sel] / x_ref[sel] - 1.0)) < 1e-3
+
+
 @pytest.mark.parametrize("dir_index", [0, 21])
 def test_full_size_single_direction(loc, oracle, dir_index):
     """128^3 grid, 11 lines, 128 channels, the launch configuration of the

@@ -112,6 +112,25 @@ def test_octree_iterations(loc, oracle):
                 assert err < 1e-4, (t, err)
 
 
+def test_octree_iterations_with_level_cutoff(loc, oracle):
+    """Per-cell line truncation on an octree: populations per leaf (down to
+    1e-20) and T_ex against the oracle's truncated iteration."""
+    mol = LI.rotor_molecule(n_levels=14)
+    model = LI.small_octree(N=4, levels=2, refine_frac=0.3, nside=2, n_ch=24, abundance=1e-4)
+    with loc.Model(model, mol) as m:
+        m.iterate(max_iter=3, window_sigmas=8.0, level_cutoff=1e-8)
+        xg = m.populations()
+        x_ref, _ = oracle.iterate_octree(mol, model, 3, level_cutoff=1e-8)
+        tref = oracle.tex(mol, x_ref)
+        for t in range(tref.shape[0]):
+            sel = x_ref[:, mol["line_u"][t]] >= 1e-6
+            if sel.any():
+                err = np.max(np.abs(m.tex(t)[sel] / tref[t, sel] - 1.0))
+                assert err < 1e-4, (t, err)
+    sel = x_ref > 1e-20
+    assert np.max(np.abs(xg[sel] / x_ref[sel] - 1.0)) < 1e-3
+
+
 def test_octree_medium_size_radiation(loc, oracle):
     """12^3 root, 3 levels, all 48 directions, 11 lines."""
     mol = LI.rotor_molecule()

@@ -67,3 +67,22 @@ def test_truncating_empty_levels_keeps_populated_lines(oracle):
     sel = x0[:, mol["line_u"]].T >= 1e-6
     assert np.max(np.abs(t1[sel] / t0[sel] - 1.0)) < 1e-9
     np.testing.assert_allclose(x1.sum(axis=1), 1.0, rtol=1e-12)
+
+
+def test_grid_and_octree_truncated_loops_reduce_to_the_plain_ones(oracle):
+    """The truncated 3D iterations (composed from the same steps as the plain
+    loops) are bit-identical to them when nothing is below the cutoff, and
+    a 1e-8 cutoff switches lines off in the 14-level rotor's cold cells."""
+    mol = LI.rotor_molecule(n_levels=14)
+    g = LI.small_grid3d(N=4, n_ch=16, nside=1, abundance=3e-4)
+    x0, d0 = oracle.iterate_grid3d(mol, g, 2)
+    x1, d1 = oracle.iterate_grid3d(mol, g, 2, level_cutoff=1e-300)
+    np.testing.assert_array_equal(x0, x1)
+    np.testing.assert_array_equal(d0, d1)
+    o = LI.small_octree(N=4, levels=2, refine_frac=0.3, nside=1, n_ch=16, abundance=1e-4)
+    y0, e0 = oracle.iterate_octree(mol, o, 2)
+    y1, e1 = oracle.iterate_octree(mol, o, 2, level_cutoff=1e-300)
+    np.testing.assert_array_equal(y0, y1)
+    np.testing.assert_array_equal(e0, e1)
+    y2, _ = oracle.iterate_octree(mol, o, 2, level_cutoff=1e-8)
+    assert oracle.line_off(mol, y2, 1e-8).mean() > 0.1
