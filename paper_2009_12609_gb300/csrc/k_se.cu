@@ -145,16 +145,20 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
         for (int j = 0; j < L; j++) M[0][j] = 1.0;
         M[0][L] = 1.0;
         for (int p = 0; p < L; p++) {
+            // magnitudes compared as the bit patterns of non-negative
+            // doubles (ordered like the values; integer compares)
             int piv = p;
-            double best = fabs(M[p][p]);
-            for (int i = p + 1; i < L; i++)
-                if (fabs(M[i][p]) > best) { best = fabs(M[i][p]); piv = i; }
+            long long best = __double_as_longlong(fabs(M[p][p]));
+            for (int i = p + 1; i < L; i++) {
+                const long long a = __double_as_longlong(fabs(M[i][p]));
+                if (a > best) { best = a; piv = i; }
+            }
             if (piv != p)
                 for (int j = p; j <= L; j++) { const double tmp = M[p][j]; M[p][j] = M[piv][j]; M[piv][j] = tmp; }
             const double inv = 1.0 / M[p][p];
             for (int i = p + 1; i < L; i++) {
                 const double f = M[i][p] * inv;
-                if (f == 0.0) continue;
+                if ((__double_as_longlong(f) << 1) == 0) continue;     // f == +-0, integer test
                 for (int j = p; j <= L; j++) M[i][j] -= f * M[p][j];
             }
         }

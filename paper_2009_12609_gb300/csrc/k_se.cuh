@@ -171,12 +171,15 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
     __syncwarp();
     double my_inv = 0.0;                                         // lane p: 1 / U[p][p]
     for (int p = 0; p < L; p++) {
-        // pivot: the first row i >= p with the largest |M[i][p]|
-        double v = (sl >= p && sl < L) ? fabs(M[sl * W + p]) : -1.0;
+        // pivot: the first row i >= p with the largest |M[i][p]|.  The
+        // magnitudes are compared as the bit patterns of non-negative doubles,
+        // which order like their values, so the search issues integer
+        // compares instead of FP64 ones; -1 marks rows outside [p, L)
+        long long v = (sl >= p && sl < L) ? __double_as_longlong(fabs(M[sl * W + p])) : -1ll;
         int idx = sl;
 #pragma unroll
         for (int off = LW / 2; off > 0; off >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+            const long long ov = __shfl_xor_sync(0xffffffffu, v, off);
             const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
             if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
         }
