@@ -422,6 +422,15 @@ loc_status loc_trace_octree(const loc_model *m, int dir, int64_t *out7, int64_t 
  * property (Sect. 2.2) makes it exactly 2^24 >> level for every leaf. */
 loc_status loc_octree_path_sums(const loc_model *m, int dir, int64_t *out, size_t n_out);
 
+/* Numerical self-check, not a step of the method: r[i] = the reciprocal
+ * that the equilibrium solve and the line parameters use in place of an FP64
+ * division (an FP32 seed refined by two Newton-Raphson steps, within about
+ * one FP64 ulp of 1 / d[i]; zero, subnormal, huge, infinite and NaN inputs
+ * give 1.0 / d[i]), evaluated on the current device.  d and r are host
+ * arrays of n doubles owned by the caller.  LOC_EINVAL for a NULL buffer
+ * with n > 0, LOC_ENOMEM / LOC_ECUDA on device failures. */
+loc_status loc_check_recip(const double *d, double *r, size_t n);
+
 /* Wait for all queued work of the model. */
 loc_status loc_sync(loc_model *m);
 

@@ -124,15 +124,16 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
                 double sj, ej;
                 if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
                 else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
-                J = sj / nrm;
-                beta = ej / nrm;
+                const double inv_nrm = recip(nrm);
+                J = sj * inv_nrm;
+                beta = ej * inv_nrm;
                 if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }
             } else {
                 J = m.nbg64[t];
                 beta = 1.0;
             }
             const double rd = A * (beta + J);
-            const double ru = (m.g[u] / m.g[l]) * A * J;
+            const double ru = m.g[u] * recip(m.g[l]) * A * J;
             M[l][u] += rd; M[l][l] -= ru;
             M[u][u] -= rd; M[u][l] += ru;
         }
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
             }
             if (piv != p)
                 for (int j = p; j <= L; j++) { const double tmp = M[p][j]; M[p][j] = M[piv][j]; M[piv][j] = tmp; }
-            const double inv = 1.0 / M[p][p];
+            const double inv = recip(M[p][p]);
             for (int i = p + 1; i < L; i++) {
                 const double f = M[i][p] * inv;
                 if ((__double_as_longlong(f) << 1) == 0) continue;     // f == +-0, integer test
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
         for (int i = L - 1; i >= 0; i--) {
             double a = M[i][L];
             for (int j = i + 1; j < L; j++) a -= M[i][j] * xs[j];
-            xs[i] = a / M[i][i];
+            xs[i] = a * recip(M[i][i]);
         }
         const double *xo = m.x + c * L;
         double *xn = m.x_new + c * L;
@@ -322,3 +323,35 @@ loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, doubl
 }
 
 }  // namespace loc
+
+namespace {
+__global__ void recip_check_kernel(const double *in, double *out, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = loc::recip(in[i]);
+}
+}  // namespace
+
+// Numerical self-check of the solve's reciprocal (see recip in k_se.cuh).
+extern "C" loc_status loc_check_recip(const double *d, double *r, size_t n)
+{
+    if (n == 0) return LOC_OK;
+    if (!d || !r) { loc::set_error("loc_check_recip: NULL buffer"); return LOC_EINVAL; }
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, 2 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        loc::set_error("loc_check_recip: device allocation failed");
+        return LOC_ENOMEM;
+    }
+    loc_status st = LOC_OK;
+    if (cudaMemcpy(buf, d, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) st = LOC_ECUDA;
+    if (st == LOC_OK) {
+        recip_check_kernel<<<(unsigned)((n + 255) / 256), 256>>>(buf, buf + n, (long long)n);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(r, buf + n, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = LOC_ECUDA;
+    }
+    if (st != LOC_OK) loc::set_error("loc_check_recip: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(buf);
+    return st;
+}

@@ -10,6 +10,32 @@ namespace loc {
 
 constexpr int kSeWarps = 4;   // warps per block of the segment-per-cell solve
 
+// 1/d in FP64 without a division (the solve is bound by FP64 instruction
+// throughput on GB300, and a division costs several FP64 instructions): the
+// exponent of d is handled as an integer, the leading 23 fraction bits get an
+// FP32 reciprocal from the SFU (rcp.approx, relative error about 2^-23), and
+// two Newton-Raphson steps r <- r + r (1 - d r) square the relative error
+// each time (2^-23 -> 2^-46 -> below the rounding of the last step), so the
+// result is within about one FP64 ulp of 1/d.  Zero, subnormal, huge,
+// infinite and NaN inputs (biased exponent outside [2, 2044]) take 1.0 / d.
+__device__ __forceinline__ double recip(double d)
+{
+    const long long b = __double_as_longlong(d);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (be < 2 || be > 2044) return 1.0 / d;
+    const float mf = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));   // mantissa in [1, 2)
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));                      // in (0.5, 1]
+    const int rb = __float_as_int(rf);
+    const long long e = (long long)(((rb >> 23) & 0xff) - 127 + 2046 - be);        // in [1, 2046]
+    double r = __longlong_as_double((b & (long long)0x8000000000000000ull) | (e << 52) |
+                                    ((long long)(rb & 0x7fffff) << 29));
+    double t = fma(-d, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-d, r, 1.0);
+    return fma(r, t, r);
+}
+
 // {K, S} of a line switched off in this cell by the truncation below
 __device__ __forceinline__ bool line_off(float2 ks)
 {
@@ -33,11 +59,11 @@ __device__ __forceinline__ void line_params_at(const DevModel &m, long long c, i
     } else if (fabs(diff) <= 1e-30 * gu * xl || (xl == 0.0 && xu == 0.0)) {
         ks = make_float2(0.f, 0.f);
     } else {
-        const double pre = kC * kC * kC * m.line_A[t] / (8.0 * kPI * nu * nu * nu * m.dv);
-        const double K = pre * m.n_h2[c] * m.abundance[c] * diff / gl;
+        const double pre = kC * kC * kC * m.line_A[t] * recip(8.0 * kPI * nu * nu * nu * m.dv * gl);
+        const double K = pre * m.n_h2[c] * m.abundance[c] * diff;
         float kf = (float)K;
         if (kf == 0.f) kf = 0.f;                    // an underflow to -0 is not the mark
-        ks = make_float2(kf, (float)(gl * xu / diff));
+        ks = make_float2(kf, (float)(gl * xu * recip(diff)));
         if (K < 0.0) atomicAdd(m.maser_count, 1ull);
     }
     m.ks[idx] = ks;
@@ -123,7 +149,7 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
     for (int i = sl; i < L * W; i += LW) M[i] = 0.0;
     __syncwarp();
     const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
-    const double inv_nrm = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+    const double inv_nrm = (nrm > 0.0) ? recip(nrm) : 0.0;
     for (int b = 0; b < m.T; b += LW) {
         const int t = b + sl;
         if (t < m.T) {
@@ -146,7 +172,7 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
                 beta = 1.0;
             }
             M[l * W + u] += A * (beta + J);                     // u -> l
-            M[u * W + l] += (m.g[u] / m.g[l]) * A * J;          // l -> u
+            M[u * W + l] += m.g[u] * recip(m.g[l]) * A * J;     // l -> u
         }
     }
     __syncwarp();
@@ -191,7 +217,7 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
             }
         }
         __syncwarp();
-        const double inv = 1.0 / M[p * W + p];
+        const double inv = recip(M[p * W + p]);
         if (sl == p) my_inv = inv;
         if (sl > p && sl < L) F[sl] = M[sl * W + p] * inv;
         __syncwarp();

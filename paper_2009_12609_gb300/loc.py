@@ -119,7 +119,7 @@ EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecul
            "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
            "loc_radiation1d_noalloc", "loc_autotune", "loc_server_create",
            "loc_server_submit", "loc_server_poll", "loc_server_stats", "loc_server_destroy",
-           "loc_trace_octree", "loc_octree_path_sums", "loc_map3d"]
+           "loc_trace_octree", "loc_octree_path_sums", "loc_map3d", "loc_check_recip"]
 
 
 def library_path():
@@ -156,6 +156,7 @@ def load():
     lib.loc_trace_ray.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                   _i64, _i64, ctypes.c_int64, _i64]
     lib.loc_sync.argtypes = [_vp]
+    lib.loc_check_recip.argtypes = [_d, _d, ctypes.c_size_t]
     lib.loc_trace_octree.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_int64, _i64]
     lib.loc_octree_path_sums.argtypes = [_vp, ctypes.c_int, _i64, ctypes.c_size_t]
     lib.loc_destroy.argtypes = [_vp]
@@ -416,6 +417,14 @@ def loc_map3d(h, t, d, level, n_pix_side, n_ch):
     out = np.zeros((int(n_pix_side) ** 2, int(n_ch)))
     _check(load().loc_map3d(h, int(t), int(d), int(level), _pd(out), out.size))
     return out
+
+
+def loc_check_recip(d):
+    """The solve's reciprocal of every element of d, evaluated on the device."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    r = np.empty_like(d)
+    _check(load().loc_check_recip(d.ctypes.data_as(_d), r.ctypes.data_as(_d), d.size))
+    return r
 
 
 def loc_trace_ray(h, d, i, j, cap=1 << 16):
