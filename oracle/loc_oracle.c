@@ -21,8 +21,10 @@
  *
  * Parity status: every function here is pinned by tests in tests/ against
  * closed forms, invariants or brute force (the per-cell line truncation by
- * tests/test_oracle_truncation.py), except the infall line shape
- * (qualitative blue asymmetry only) -- see the test module docstrings.
+ * tests/test_oracle_truncation.py), except the asymmetry of infall lines
+ * from excitation gradients (qualitative blue asymmetry only; the Doppler
+ * geometry is pinned by a homologous-infall closed form) -- see the test
+ * module docstrings.
  */
 #include <math.h>
 #include <stdint.h>

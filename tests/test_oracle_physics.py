@@ -18,11 +18,16 @@ What fixes each part (Sect. 2 of the paper for the method):
     uniform cube crossed along an axis gives closed-form J_ext and beta.
   * ALI (Sect. 2): same fixed point as lambda iteration, fewer iterations
     when optically thick; thermalisation at high density.
-Parity unpinned: the infall line shape (qualitative blue asymmetry only).
+  * Velocity field: a homologously collapsing uniform sphere converges to
+    the closed-form spectrum of its line-of-sight velocity distribution.
+Parity unpinned: the asymmetry of infall lines from excitation gradients
+(qualitative blue asymmetry only; the Doppler geometry itself is pinned by
+the homologous-infall closed form).
 """
 import numpy as np
 import pytest
 from scipy import integrate
+from scipy.special import erf
 
 import loc_inputs as LI
 
@@ -235,6 +240,49 @@ def test_high_density_thermalises(oracle):
     bound = mol["line_A"].max() / (m["n_h2"].min() * mol["coll_k"].max())
     assert bound < 2e-5
     np.testing.assert_allclose(x, oracle.lte_populations(mol, m["t_kin"]), rtol=5 * bound)
+
+
+def _int_erf(x):
+    """Antiderivative of erf: x erf(x) + exp(-x^2) / sqrt(pi)."""
+    return x * erf(x) + np.exp(-x * x) / np.sqrt(np.pi)
+
+
+def test_homologous_infall_spectrum_converges_to_closed_form(oracle):
+    """Velocity field along the rays: a uniform sphere in homologous infall,
+    v(r) = -v0 r / R, has v_los = -v0 z / R along every chord (z from the
+    chord's midpoint), so with uniform K and S the emergent intensity is
+    n_bg e^-tau + S (1 - e^-tau) with tau_k = K (R / v0) times the integral
+    of channel k's Gaussian fraction over line centres in [-V, V], V = v0
+    (half chord) / R -- a closed form through the antiderivative of erf.
+    The shells hold v at their mid radius and each step takes v_los at its
+    entry point, so the spectra converge to it as the shells get thinner."""
+    mol = LI.two_level_molecule()
+    nu = mol["line_nu"][0]
+    errs = []
+    for K in (64, 512, 4096):
+        m = LI.uniform_sphere(K=K, n_ch=48, abundance=2e-10, half_width_kms=2.0)
+        R, v0 = m["radius"][-1], 0.6e5
+        m["v"] = -v0 * (np.arange(K) + 0.5) / K
+        x = np.tile(np.array([0.4, 0.6]), (K, 1))
+        p = np.array([0.0, 0.3, 0.7, 0.95]) * R
+        T = oracle.spectra_1d(mol, m, x, 0, p)
+        Kp, S = oracle.line_params(mol, m, x)
+        sig = np.sqrt(m["sigma_turb"][0] ** 2 + KB * m["t_kin"][0] / (mol["mass_amu"] * AMU))
+        s2 = np.sqrt(2.0) * sig
+        e = m["v_min"] + np.arange(m["n_ch"] + 1) * m["dv"]
+        nbg = planck_occ(nu, m["t_bg"])
+        ref = []
+        for pp in p:
+            V = v0 * np.sqrt(R * R - pp * pp) / R
+            frac = 0.5 * s2 * (_int_erf((e[1:] + V) / s2) - _int_erf((e[1:] - V) / s2)
+                               - _int_erf((e[:-1] + V) / s2) + _int_erf((e[:-1] - V) / s2))
+            tau = Kp[0, 0] * (R / v0) * frac
+            n = nbg * np.exp(-tau) - S[0, 0] * np.expm1(-tau)
+            ref.append(H * nu / KB * (n - nbg))
+        ref = np.array(ref)
+        errs.append(np.abs(T - ref).max() / np.abs(ref).max())
+    assert errs[0] > 3.0 * errs[1] > 9.0 * errs[2], errs
+    assert errs[2] < 3e-3, errs
 
 
 def test_infall_blue_asymmetry_qualitative(oracle):
