@@ -667,10 +667,10 @@ loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int
     }
     // timed with the per-cell line truncation the iterations will use
     TRY(launch_line_params(m->d, m->st, 0, o->level_cutoff));
-    m->d.trunc = o->level_cutoff > 0.0 ? 1 : 0;
     cudaEvent_t e0, e1;
     LOC_CUDA_TRY(cudaEventCreate(&e0));
     LOC_CUDA_TRY(cudaEventCreate(&e1));
+    m->d.trunc = o->level_cutoff > 0.0 ? 1 : 0;        // reset below on every path
     int best = cand[0], best_run = -1;
     float best_t = 1e30f;
     loc_iter_opts oo = *o;
