@@ -42,16 +42,18 @@ def test_struct_layouts_match_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "loc.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(loc_model_desc), sizeof(loc_molecule_desc), sizeof(loc_iter_opts),"
         "sizeof(loc_iter_report), offsetof(loc_model_desc, allocator),"
-        "offsetof(loc_molecule_desc, coll_k));return 0;}\n")
+        "offsetof(loc_molecule_desc, coll_k), offsetof(loc_model_desc, ray_power),"
+        "offsetof(loc_iter_opts, level_cutoff));return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     exp = [ctypes.sizeof(loc.loc_model_desc), ctypes.sizeof(loc.loc_molecule_desc),
            ctypes.sizeof(loc.loc_iter_opts), ctypes.sizeof(loc.loc_iter_report),
-           loc.loc_model_desc.allocator.offset, loc.loc_molecule_desc.coll_k.offset]
+           loc.loc_model_desc.allocator.offset, loc.loc_molecule_desc.coll_k.offset,
+           loc.loc_model_desc.ray_power.offset, loc.loc_iter_opts.level_cutoff.offset]
     assert out == exp
 
 
@@ -60,4 +62,6 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.loc_create_model(None, None) == loc.LOC_EINVAL
     assert "NULL" in loc.loc_last_error()
     assert lib.loc_iterate(None, None, None) == loc.LOC_EINVAL
+    assert lib.loc_check_recip(None, None, 1) == loc.LOC_EINVAL
+    assert lib.loc_check_recip(None, None, 0) == loc.LOC_OK
     lib.loc_destroy(None)
