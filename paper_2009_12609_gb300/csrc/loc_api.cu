@@ -412,9 +412,14 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
     TRY(upload<unsigned long long>(m, &D.maser_count, nullptr, 1, m->mol_mem, "maser count"));
     TRY(upload<unsigned long long>(m, &D.upd_count, nullptr, 1, m->mol_mem, "update count"));
     // collision rates depend only on n_H2 and T_kin: tabulated once when the
-    // table is modest (<= 4M entries), else computed inside every solve
+    // table (16 B per cell and pair) takes at most a quarter of the free
+    // device memory and 16 GiB, else computed inside every solve (an FP64
+    // exponential per pair and cell, the costliest part of a large solve)
     D.coll_rates = nullptr;
-    if (D.P > 0 && nc * D.P <= (1ll << 22)) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    const double table_b = 16.0 * (double)nc * (double)D.P;
+    if (D.P > 0 && table_b <= std::min(0.25 * (double)free_b, 16.0 * (1ull << 30))) {
         TRY(upload<double2>(m, &D.coll_rates, nullptr, nc * D.P, m->mol_mem, "collision rates"));
         TRY(launch_coll_rates(D, D.coll_rates, m->st));
     }
