@@ -44,7 +44,7 @@ struct ArenaLayout {
     size_t n_h2, t_kin, abundance, sigma, radius, v1d, energy, g, line_u, line_l, line_A, line_nu,
         coll_u, coll_l, coll_k;       // uploaded inputs (contiguous prefix)
     size_t inputs_end;
-    size_t inv, ray_off, segs, tan, W, nbg, nbg64, x, x_new, ks, acc, norm, dtex, maser, upd;
+    size_t inv, ray_off, segs, tan, W, nbg, nbg64, x, x_new, ks, acc, norm, dtex, maser, upd, coll;
     size_t total;
 };
 
@@ -94,6 +94,7 @@ static ArenaLayout layout_for(const Request &q)
     a.tan = put(4 * R); a.W = put(8 * K); a.nbg = put(4 * T); a.nbg64 = put(8 * T);
     a.x = put(8 * K * L); a.x_new = put(8 * K * L); a.ks = put(8 * K * T); a.acc = put(8 * K * T);
     a.norm = put(4 * K); a.dtex = put(4); a.maser = put(8); a.upd = put(8);
+    a.coll = put(16 * K * (P ? P : 1));   // collision rates per cell and pair, tabulated once
     a.total = o;
     return a;
 }
@@ -300,9 +301,11 @@ static bool admit(loc_server *s, int si, Request *q)
     m.dtex_bits = (unsigned *)(b + a.dtex);
     m.maser_count = (unsigned long long *)(b + a.maser);
     m.upd_count = (unsigned long long *)(b + a.upd);
+    m.coll_rates = q->P > 0 ? (double2 *)(b + a.coll) : nullptr;
     if (cudaMemsetAsync(m.dtex_bits, 0, 4, s->st) != cudaSuccess) return false;
     if (launch_geom1d_scratch(m, s->st, (int *)(b + a.tan), (double *)(b + a.W)) != LOC_OK) return false;
     if (launch_cell_setup(m, (const double *)(b + a.sigma), nullptr, nullptr, nullptr, s->st) != LOC_OK) return false;
+    if (m.coll_rates && launch_coll_rates(m, m.coll_rates, s->st) != LOC_OK) return false;
     if (launch_bg(m, s->st) != LOC_OK) return false;
     if (launch_lte(m, s->st) != LOC_OK) return false;
     // lines per warp: per x n_ch <= 2048 floats of shared memory, rounded
