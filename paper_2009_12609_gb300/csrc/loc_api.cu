@@ -730,7 +730,6 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     TRY(check_opts(o));
     if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
     DevModel &D = m->d;
-    D.trunc = o->level_cutoff > 0.0 ? 1 : 0;
     const bool prof = o->profile == 1;
     std::vector<cudaEvent_t> ev;              // 4 per iteration when profiling
     auto mark = [&](size_t idx) -> cudaError_t {
@@ -753,6 +752,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     float dtex = 0.f;
     bool converged = false;
     const bool fuse = !(o->tol_tex > 0.0);
+    D.trunc = o->level_cutoff > 0.0 ? 1 : 0;           // reset after the loop on every path
     loc_status st = LOC_OK;
     // NVTX ranges mark the host-side phases of every iteration for timeline
     // tools (no cost without an attached tool)
