@@ -170,7 +170,7 @@ typedef struct loc_molecule_desc {
  *                 whole-ray march up to rounding.  Ignored for 3D models.
  *  level_cutoff   per-cell line truncation in the ALI loop (the paper's
  *                 suggestion to skip, cell by cell, transitions between
- *                 levels that are not populated, Sect. 5): 0 = off; c > 0:
+ *                 levels that are not populated, Sect. 4): 0 = off; c > 0:
  *                 in a cell where both levels of a line hold less than c of
  *                 the molecules, the line is left out of that iteration's
  *                 ray simulation there (its opacity is taken as zero) and

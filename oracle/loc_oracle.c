@@ -377,7 +377,7 @@ static int lo_gauss_solve(int n, double *M, double *b)
     return 0;
 }
 
-/* Per-cell line truncation (Sect. 5 proposes computing, cell by cell, only   */
+/* Per-cell line truncation (Sect. 4 proposes computing, cell by cell, only   */
 /* the transitions whose levels are populated, without giving a rule; this   */
 /* is our reading): line t is off in cell c when both of its levels hold     */
 /* less than `cutoff` of the molecules, off[t][c] = 1.  An off line has no   */

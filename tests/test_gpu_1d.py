@@ -264,7 +264,7 @@ def test_power_law_rays_match_oracle(loc, oracle, ray_power, steps_per_chunk):
 
 
 def test_level_cutoff_truncates_lines_within_tolerance(loc, oracle):
-    """Per-cell line truncation (the paper's suggested optimisation, Sect. 5):
+    """Per-cell line truncation (the paper's suggested optimisation, Sect. 4):
     lines whose two levels are empty in a cell are left out there.  The
     populations match the oracle's truncated iteration level by level (down
     to 1e-20), the monitored excitation temperatures also match the

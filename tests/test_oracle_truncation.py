@@ -1,4 +1,4 @@
-"""Pins of the oracle's per-cell line truncation (Sect. 5 proposes computing,
+"""Pins of the oracle's per-cell line truncation (Sect. 4 proposes computing,
 cell by cell, only the transitions whose levels are populated; the rule --
 a line is off in a cell when both of its levels hold less than the cutoff,
 and an off line has no opacity there and takes the background field,
