@@ -97,6 +97,13 @@ typedef struct loc_allocator {
  *               equidistant rays (the default), > 1 concentrates rays towards
  *               the centre (small inner shells), (0, 1) towards the edge;
  *               at most 10.
+ *  octree_paths octree: 0 (default) records the paths of all rays once,
+ *               at creation (8 bytes per active ray step or intensity copy
+ *               of the split / side-ray rules of Sect. 2.2), when they fit
+ *               in device memory, and every ray simulation replays them;
+ *               1 walks the tree in every ray simulation (no records).  The
+ *               results are the same either way: the replay applies the
+ *               same steps, in the same order, as the walk.
  */
 typedef struct loc_model_desc {
     int geometry;
@@ -119,6 +126,7 @@ typedef struct loc_model_desc {
     void *stream;
     const loc_allocator *allocator;
     double ray_power;
+    int octree_paths;
 } loc_model_desc;
 
 /*
@@ -207,6 +215,11 @@ typedef struct loc_iter_report {
     double params_ms;          /* summed duration of the line-parameter step*/
     int64_t march_launches;    /* number of march launches                  */
     double computed_updates;   /* updates inside the channel windows        */
+    /* how the work was done (always filled) */
+    int64_t path_records;      /* octree: recorded path records the march
+                                  replays (0: it walks the tree)             */
+    int coll_table;            /* 1: collision rates read from the model's
+                                  table; 0: recomputed in every solve       */
 } loc_iter_report;
 
 typedef struct loc_model loc_model;

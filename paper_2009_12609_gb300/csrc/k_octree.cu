@@ -26,12 +26,15 @@
 // a refined cell are examined one per lane (entry point, and whether the line
 // was inactive just before -- one octree descent each) and collected with a
 // ballot; point location is an integer descent through the child array.
+#include <algorithm>
+
 #include "k_march.cuh"
 
 namespace loc {
 
 constexpr int kOctWarpsPerBlock = 4;
 constexpr int kOctBlocksPerSM = 4;
+constexpr int kOctMaxBlocksPerSM = 8;       // replay: up to 32 warps per SM
 constexpr int kOctMaxDepth = 10;
 
 // floor(n / q) with minv = floor((2^64 - 1) / q): one correction step
@@ -235,8 +238,41 @@ __device__ __forceinline__ void oct_spawn(const DevModel &m, const OctGeo &g, co
     nk += __popc(mask);
 }
 
+// Path records of a root-ray family, in the order of the depth-first
+// traversal: one 64-bit word per active step or intensity copy.
+//   step:  leaf (bits 0-31), dz (bits 32-56, at most 2^24), leaf level
+//          (bits 57-60), type 0 (bits 61-63)
+//   save:  type 1, frame depth in bits 0-31 (snapshot I before new rays)
+//   load:  type 2, frame depth in bits 0-31 (I from that snapshot: the start
+//          of a new ray, or the creating line resuming)
+constexpr unsigned kRecStep = 0, kRecSave = 1, kRecLoad = 2;
+
+__device__ __forceinline__ unsigned long long rec_step(int leaf, long long dz, int level)
+{
+    return (unsigned long long)(unsigned)leaf | ((unsigned long long)dz << 32) |
+           ((unsigned long long)level << 57);
+}
+
+__device__ __forceinline__ unsigned long long rec_ctrl(unsigned type, int depth)
+{
+    return (unsigned long long)(unsigned)depth | ((unsigned long long)type << 61);
+}
+
+// Weight of a step of main-axis length dz through a level-L leaf, dz / H_L
+// / n_dir (H_L = 2^(24 - L) units): the division by a power of two is exact,
+// so it is a multiplication by 2^(L - 24).
+__device__ __forceinline__ float oct_weight(long long dz, int L, float wscale)
+{
+    return (float)(int)dz * __int_as_float((127 + L - kFixedBits) << 23) * wscale;
+}
+
+// Visitors of the traversal: the march applies each step to the warp's
+// intensities (kNeedI); the others only see the geometry.
 struct OctMarchVisitor {
     static constexpr bool kNeedI = true;
+    __device__ void step(int, const OctLine &, long long, int, int) {}
+    __device__ void save(int, int) {}
+    __device__ void load(int, int) {}
 };
 
 struct OctTraceVisitor {
@@ -247,6 +283,42 @@ struct OctTraceVisitor {
     unsigned long long *sums;  // optional per-leaf sum of dz
     int dir;
     unsigned local;            // active steps of the current family
+    unsigned ctrl;             // intensity copies (saves and loads) of the family
+    __device__ void step(int lane, const OctLine &cur, long long dz, int leaf, int Lc)
+    {
+        local++;
+        if (lane == 0) {
+            if (sums) atomicAdd(sums + leaf, (unsigned long long)dz);
+            if (count) {
+                const unsigned long long n = atomicAdd(count, 1ull);
+                if ((long long)n < cap) {
+                    long long *o = out + 7 * n;
+                    o[0] = cur.lam; o[1] = cur.i; o[2] = cur.j; o[3] = cur.z; o[4] = dz;
+                    o[5] = leaf; o[6] = Lc;
+                }
+            }
+        }
+    }
+    __device__ void save(int, int) { ctrl++; }
+    __device__ void load(int, int) { ctrl++; }
+};
+
+// Writes the path records of one family to rec[0 .. n).
+struct OctRecVisitor {
+    static constexpr bool kNeedI = false;
+    unsigned long long *rec;
+    long long n, cap;
+    __device__ void put(int lane, unsigned long long w)
+    {
+        if (lane == 0 && n < cap) rec[n] = w;
+        n++;
+    }
+    __device__ void step(int lane, const OctLine &, long long dz, int leaf, int Lc)
+    {
+        put(lane, rec_step(leaf, dz, Lc));
+    }
+    __device__ void save(int lane, int depth) { put(lane, rec_ctrl(kRecSave, depth)); }
+    __device__ void load(int lane, int depth) { put(lane, rec_ctrl(kRecLoad, depth)); }
 };
 
 // Depth-first traversal of the rays created from root line (i, j).
@@ -258,6 +330,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
     const long long H0 = 1ll << kFixedBits;
     const int snap_n = a.per * m.n_ch;
     const float wscale = 1.0f / (float)m.n_dir;
+    (void)wscale;
     OctLine cur = {0, i, j, 0};
     long long skip_z = -1;          // a resumed line does not create rays twice at one face
     int depth = 0;
@@ -306,6 +379,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                         float *sn = snap + (size_t)depth * snap_n;
                         for (int q = lane; q < snap_n; q += 32) sn[q] = I[q];
                     }
+                    vis.save(lane, depth);
                     depth++;
                     __syncwarp();
                     done_line = true;                       // switch to the first new ray below
@@ -335,21 +409,12 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                 st.vlos = cv.x * g.D.d[0] + cv.y * g.D.d[1] + cv.z * g.D.d[2];
                 st.inv = cv.w;
                 st.s = (float)(int)dz * g.D.unit;       // dz <= one leaf <= 2^24 units
-                st.w = (float)(int)dz / (float)(int)HL * wscale;
+                st.w = oct_weight(dz, Lc, wscale);
                 load_lines<G>(m, a, st);
                 nw += (long long)march_step<G>(m, a, I, st, lane) * a.n_lines;
                 __syncwarp();
             } else {
-                vis.local++;
-                if (lane == 0) {
-                    if (vis.sums) atomicAdd(vis.sums + leaf, (unsigned long long)dz);
-                    const unsigned long long n = atomicAdd(vis.count, 1ull);
-                    if ((long long)n < vis.cap) {
-                        long long *o = vis.out + 7 * n;
-                        o[0] = cur.lam; o[1] = cur.i; o[2] = cur.j; o[3] = cur.z; o[4] = dz;
-                        o[5] = leaf; o[6] = Lc;
-                    }
-                }
+                vis.step(lane, cur, dz, leaf, Lc);
             }
             cur.z = zn;
             skip_z = -1;
@@ -378,6 +443,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
             const float *src = snap + (size_t)fi * snap_n;
             for (int q = lane; q < snap_n; q += 32) I[q] = src[q];
         }
+        vis.load(lane, fi);
         __syncwarp();
     }
 }
@@ -421,10 +487,34 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
     if (a0.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)nw);   // nw counts lines
 }
 
+// Geometry of a traversal without intensities (tracing and recording).
+__device__ __forceinline__ OctGeo oct_geo(const DevModel &m)
+{
+    OctGeo g;
+    g.N = m.N;
+    g.Lmax = m.Lmax;
+    g.E = (long long)m.N << kFixedBits;
+    g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
+    return g;
+}
+
+__device__ __forceinline__ MarchArgs oct_geo_args()
+{
+    MarchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.per = 1;
+    a.n_groups = 1;
+    a.n_lines = 1;
+    return a;
+}
+
+// fam_work[f]: active steps of family f; fam_rec[f]: its path records
+// (steps, saves and loads); either may be null.
 __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(DevModel m, int dir,
                                                                                OctTraceVisitor vis,
                                                                                unsigned *counter,
-                                                                               unsigned *fam_work)
+                                                                               unsigned *fam_work,
+                                                                               unsigned *fam_rec)
 {
     __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
     __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
@@ -433,17 +523,9 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
     const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
     int4 *kids = m.oct_kids + (size_t)gw * kOctMaxDepth * kOctMaxKids;
     const long long per_dir = (long long)m.N * m.N;
-    MarchArgs a;
-    memset(&a, 0, sizeof(a));
-    a.per = 1;
-    a.n_groups = 1;
-    a.n_lines = 1;
+    const MarchArgs a = oct_geo_args();
     long long nw = 0;
-    OctGeo g;
-    g.N = m.N;
-    g.Lmax = m.Lmax;
-    g.E = (long long)m.N << kFixedBits;
-    g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
+    OctGeo g = oct_geo(m);
     // dir >= 0: the root lines of that direction; dir < 0: of every direction
     const long long total = dir >= 0 ? per_dir : per_dir * m.n_dir;
     while (true) {
@@ -455,10 +537,148 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
         const long long r = dir >= 0 ? (long long)it : (long long)it - (long long)d * per_dir;
         g.D = m.dirs[d];
         vis.local = 0;
+        vis.ctrl = 0;
         oct_traverse<1>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
                         paths[wid], lane, vis, nw);
         if (fam_work && lane == 0) fam_work[(long long)d * per_dir + r] = vis.local;
+        if (fam_rec && lane == 0) fam_rec[(long long)d * per_dir + r] = vis.local + vis.ctrl;
     }
+}
+
+// Path records of every family f (direction f / N^2, root line f % N^2) at
+// m.oct_rec + m.oct_rec_off[f], by the traversal the march uses.  A family
+// whose record count differs from its slot raises error flag 4.
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) record_octree_kernel(DevModel m, unsigned *counter)
+{
+    __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
+    __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
+    int4 *kids = m.oct_kids + (size_t)gw * kOctMaxDepth * kOctMaxKids;
+    const long long per_dir = (long long)m.N * m.N;
+    const MarchArgs a = oct_geo_args();
+    long long nw = 0;
+    OctGeo g = oct_geo(m);
+    const long long total = per_dir * m.n_dir;
+    while (true) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if ((long long)it >= total) break;
+        const int d = (int)((long long)it / per_dir);
+        const long long r = (long long)it - (long long)d * per_dir;
+        g.D = m.dirs[d];
+        OctRecVisitor vis;
+        const long long r0 = m.oct_rec_off[it];
+        vis.rec = m.oct_rec + r0;
+        vis.cap = m.oct_rec_off[it + 1] - r0;
+        vis.n = 0;
+        oct_traverse<1>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
+                        paths[wid], lane, vis, nw);
+        if (vis.n != vis.cap && lane == 0) atomicExch(m.oct_err, 4);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Replay of the recorded paths: the march without the traversal.  A warp
+// takes (family, line group) items in decreasing order of work, streams the
+// family's records (32 per coalesced load, broadcast by shuffle) and applies
+// each step with march_step; save / load records copy the intensities to or
+// from the warp's snapshot frames exactly where the traversal does, so every
+// step sees the intensities the walking march gives it.  The next step's
+// cell data is loaded while the current step computes.
+// ----------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ void replay_load(const DevModel &m, const MarchArgs &a, const Dir3D &D,
+                                            float wscale, unsigned long long x, Step<G> &st)
+{
+    const int leaf = (int)(unsigned)(x & 0xffffffffull);
+    const long long dz = (long long)((x >> 32) & 0x1ffffffull);
+    const int Lc = (int)((x >> 57) & 0xfull);
+    st.cell = leaf;
+    const float4 cv = m.vel[leaf];
+    st.vlos = cv.x * D.d[0] + cv.y * D.d[1] + cv.z * D.d[2];
+    st.inv = cv.w;
+    st.s = (float)(int)dz * D.unit;
+    st.w = oct_weight(dz, Lc, wscale);
+    load_lines<G>(m, a, st);
+}
+
+template <int G>
+__device__ long long replay_family(const DevModel &m, const MarchArgs &a, const Dir3D &D, long long r0,
+                                   long long r1, float *I, float *snap, int lane)
+{
+    const unsigned long long *rec = m.oct_rec;
+    const int snap_n = a.per * m.n_ch;
+    const float wscale = 1.0f / (float)m.n_dir;
+    long long nw = 0;
+    long long b0 = r0;                                   // first record of the current block
+    unsigned long long rb = (b0 + lane < r1) ? rec[b0 + lane] : 0ull;
+    unsigned long long rn = (b0 + 32 + lane < r1) ? rec[b0 + 32 + lane] : 0ull;
+    Step<G> cur, nxt;
+    bool pre = false;                                    // cur holds the data of record q
+    for (long long q = r0; q < r1; q++) {
+        if (q - b0 == 32) {
+            b0 += 32;
+            rb = rn;
+            rn = (b0 + 32 + lane < r1) ? rec[b0 + 32 + lane] : 0ull;
+        }
+        const int r = (int)(q - b0);
+        const unsigned long long x = __shfl_sync(kFull, rb, r);
+        const unsigned long long y1 = __shfl_sync(kFull, rb, (r + 1) & 31);
+        const unsigned long long y2 = __shfl_sync(kFull, rn, 0);
+        const unsigned long long y = (r < 31) ? y1 : y2;
+        const unsigned type = (unsigned)(x >> 61);
+        if (type == kRecStep) {
+            if (!pre) replay_load<G>(m, a, D, wscale, x, cur);
+            const bool nstep = (q + 1 < r1) && ((unsigned)(y >> 61) == kRecStep);
+            if (nstep) replay_load<G>(m, a, D, wscale, y, nxt);
+            nw += (long long)march_step<G>(m, a, I, cur, lane) * a.n_lines;
+            __syncwarp();
+            if (nstep) cur = nxt;
+            pre = nstep;
+        } else {
+            const int depth = (int)(unsigned)(x & 0xffffffffull);
+            float *sn = snap + (size_t)depth * snap_n;
+            if (type == kRecSave) {
+                for (int k = lane; k < snap_n; k += 32) sn[k] = I[k];
+            } else {
+                for (int k = lane; k < snap_n; k += 32) I[k] = sn[k];
+            }
+            __syncwarp();
+            pre = false;
+        }
+    }
+    return nw;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) replay_octree_kernel(DevModel m, MarchArgs a0,
+                                                                                unsigned *counter)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
+    float *I = smem + (size_t)wid * a0.per * m.n_ch;
+    float *snap = m.oct_scratch + (size_t)gw * kOctMaxDepth * a0.per * m.n_ch;
+    const long long per_dir = (long long)m.N * m.N;
+    const long long total = per_dir * m.n_dir * a0.n_groups;
+    long long nw = 0;
+    while (true) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if ((long long)it >= total) break;
+        const long long fam = (long long)it / a0.n_groups;     // most work first
+        const long long item = m.oct_order ? (long long)m.oct_order[fam] : fam;
+        const MarchArgs a = warp_args(m, a0, (int)((long long)it - fam * a0.n_groups));
+        const Dir3D D = m.dirs[item / per_dir];
+        init_ray<G>(m, a, I, lane);
+        nw += replay_family<G>(m, a, D, m.oct_rec_off[item], m.oct_rec_off[item + 1], I, snap, lane);
+    }
+    if (a0.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)nw);   // nw counts lines
 }
 
 // ----------------------------------------------------------------------------
@@ -544,25 +764,57 @@ loc_status launch_map_octree(const DevModel &m, int t, int dir, int lam, float *
     return launch_map_oct_c<34>(m, t, dir, lam, T_dev, st);
 }
 
-int octree_persistent_warps(const DevModel &m)
+static int octree_sms()
 {
-    (void)m;
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
         cudaGetLastError();
         nsm = 152;
     }
-    return nsm * kOctBlocksPerSM * kOctWarpsPerBlock;
+    return nsm;
+}
+
+// warps of the walking kernels, and the most warps any octree march launches
+// (the per-warp snapshot scratch is sized for it)
+int octree_persistent_warps(const DevModel &m)
+{
+    (void)m;
+    return octree_sms() * kOctBlocksPerSM * kOctWarpsPerBlock;
+}
+
+int octree_max_warps(const DevModel &m)
+{
+    (void)m;
+    return octree_sms() * kOctMaxBlocksPerSM * kOctWarpsPerBlock;
+}
+
+// persistent blocks per SM of a march kernel: what the occupancy calculator
+// allows (registers, shared memory), at least kOctBlocksPerSM
+template <class K>
+static int oct_blocks_per_sm(K kernel, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kOctWarpsPerBlock * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 0;
+    }
+    return std::max(kOctBlocksPerSM, std::min(nb, kOctMaxBlocksPerSM));
 }
 
 template <int G>
 static loc_status launch_oct_g(const DevModel &m, const MarchArgs &a, unsigned *counter, cudaStream_t st)
 {
     const size_t smem = (size_t)kOctWarpsPerBlock * a.per * m.n_ch * sizeof(float);
-    LOC_CUDA_TRY(cudaFuncSetAttribute(march_octree_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
-    march_octree_kernel<G><<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+    if (m.oct_rec) {
+        LOC_CUDA_TRY(cudaFuncSetAttribute(replay_octree_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int blocks = octree_sms() * oct_blocks_per_sm(replay_octree_kernel<G>, smem);
+        replay_octree_kernel<G><<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+    } else {
+        LOC_CUDA_TRY(cudaFuncSetAttribute(march_octree_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
+        march_octree_kernel<G><<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+    }
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }
@@ -593,19 +845,31 @@ loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream
 
 loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,
                                unsigned long long *count, cudaStream_t st, unsigned long long *sums,
-                               unsigned *fam_work)
+                               unsigned *fam_work, unsigned *fam_rec)
 {
     unsigned *counter = (unsigned *)(m.oct_err + 1);
     LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-    LOC_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+    if (count) LOC_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
     OctTraceVisitor vis;
     vis.out = out;
     vis.cap = cap;
     vis.count = count;
     vis.sums = sums;
     vis.dir = dir;
+    vis.local = 0;
+    vis.ctrl = 0;
     const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
-    trace_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, dir, vis, counter, fam_work);
+    trace_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, dir, vis, counter, fam_work, fam_rec);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_record_octree(const DevModel &m, cudaStream_t st)
+{
+    unsigned *counter = (unsigned *)(m.oct_err + 1);
+    LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
+    record_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, counter);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

@@ -62,6 +62,8 @@ struct loc_model {
     std::vector<void *> run_mem, run_ab_mem;
     size_t oct_scratch_floats = 0;   // octree traversal scratch currently allocated
     std::vector<void *> oct_mem;
+    long long path_records = 0;      // octree: recorded path records (0: the march walks the tree)
+    std::vector<void *> path_mem;
 };
 
 static void *dev_alloc(loc_model *m, size_t bytes, std::vector<void *> &owner)
@@ -136,6 +138,42 @@ const char *loc_last_error(void) { return g_err; }
 
 const char *loc_version(void) { return "loc-gb300 0.1 (sm_103a)"; }
 
+// Records of the octree paths (see record_octree_kernel): offsets from the
+// per-family record counts, one device buffer for all records, filled by one
+// traversal.  A failed allocation leaves the model walking the tree.
+static loc_status record_octree_paths(loc_model *m, const std::vector<unsigned> &nrec)
+{
+    DevModel &D = m->d;
+    const size_t fams = nrec.size();
+    std::vector<long long> off(fams + 1, 0);
+    for (size_t f = 0; f < fams; f++) off[f + 1] = off[f] + nrec[f];
+    const long long total = off[fams];
+    unsigned long long *rec = (unsigned long long *)dev_alloc(m, sizeof(unsigned long long) * (size_t)std::max(total, 1ll), m->path_mem);
+    if (!rec) {
+        m->path_records = 0;
+        return LOC_OK;
+    }
+    long long *offd = (long long *)dev_alloc(m, sizeof(long long) * (fams + 1), m->path_mem);
+    if (!offd) {
+        dev_free_all(m, m->path_mem);
+        m->path_records = 0;
+        return LOC_OK;
+    }
+    LOC_CUDA_TRY(cudaMemcpyAsync(offd, off.data(), sizeof(long long) * (fams + 1), cudaMemcpyHostToDevice, m->st));
+    D.oct_rec = rec;
+    D.oct_rec_off = offd;
+    TRY(launch_record_octree(D, m->st));
+    int flag = 0;
+    LOC_CUDA_TRY(cudaMemcpyAsync(&flag, D.oct_err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    if (flag) {
+        set_error("recording the octree paths failed (code %d)", flag);
+        return LOC_ECUDA;
+    }
+    m->path_records = total;
+    return LOC_OK;
+}
+
 static loc_status create_impl(loc_model *m, const loc_model_desc *d)
 {
     DevModel &D = m->d;
@@ -189,6 +227,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             CHECK(std::isfinite(n2) && fabs(n2 - 1.0) < 1e-6, "direction %d is not a unit vector", i);
         }
         CHECK(d->octree_levels >= 0 && d->octree_levels <= 10, "octree_levels must be in [0, 10]");
+        CHECK(d->octree_paths == 0 || d->octree_paths == 1, "octree_paths must be 0 or 1");
         CHECK(d->octree_refine && d->vx && d->vy && d->vz, "octree model needs refine flags and velocities");
         const long long N3 = (long long)d->n_root * d->n_root * d->n_root;
         CHECK(d->octree_n_cells >= N3 && d->octree_n_cells < (1ll << 31), "octree_n_cells out of range");
@@ -299,18 +338,25 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             // the families in order of decreasing work (fewer idle warps at
             // the end of a persistent launch)
             const long long fams = (long long)D.N * D.N * D.n_dir;
-            unsigned *work = nullptr;
+            unsigned *work = nullptr, *nrec = nullptr;
             TRY(upload<unsigned>(m, &work, nullptr, fams, m->geo_mem, "family work"));
-            TRY(launch_trace_octree(D, -1, nullptr, 0, cnt, m->st, nullptr, work));
+            TRY(upload<unsigned>(m, &nrec, nullptr, fams, m->geo_mem, "family records"));
+            TRY(launch_trace_octree(D, -1, nullptr, 0, cnt, m->st, nullptr, work, nrec));
             LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
             LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
-            std::vector<unsigned> wh(fams);
+            std::vector<unsigned> wh(fams), rh(fams);
             LOC_CUDA_TRY(cudaMemcpy(wh.data(), work, sizeof(unsigned) * fams, cudaMemcpyDeviceToHost));
+            LOC_CUDA_TRY(cudaMemcpy(rh.data(), nrec, sizeof(unsigned) * fams, cudaMemcpyDeviceToHost));
             std::vector<int> order(fams);
             for (long long f = 0; f < fams; f++) order[f] = (int)f;
             std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wh[x] > wh[y]; });
             TRY(upload(m, &D.oct_order, order.data(), fams, m->geo_mem, "family order"));
             LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+            // the paths never change: record them once (8 bytes per step or
+            // intensity copy) and let every ray simulation replay them,
+            // unless the caller asked to walk the tree or the records do not
+            // fit in device memory
+            if (d->octree_paths == 0) TRY(record_octree_paths(m, rh));
         } else {
             TRY(launch_count3d(D, cnt, m->st));
             LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
@@ -497,9 +543,10 @@ static int lines_per_warp(const loc_model *m, const loc_iter_opts *o)
     if (o->lines_per_pass == 0) {
         const long long items = (D.geometry == LOC_SHELLS_1D) ? (long long)D.n_rays
                                                               : (long long)D.N * D.N * D.n_dir;
-        // octree: at most 6 lines share one traversal (measured best on the
-        // 32^3- and 64^3-root clouds; more lines per warp cost occupancy)
-        if (D.geometry == LOC_OCTREE_3D && per > 6) per = (D.T + (D.T + 5) / 6 - 1) / ((D.T + 5) / 6);
+        // octree walked in every march: at most 6 lines share one traversal
+        // (measured best on the 32^3- and 64^3-root clouds; more lines per
+        // warp cost occupancy); replayed paths carry every line per warp
+        if (D.geometry == LOC_OCTREE_3D && !D.oct_rec && per > 6) per = (D.T + (D.T + 5) / 6 - 1) / ((D.T + 5) / 6);
         const long long target = 32ll * m->n_sm;
         while (per > 1 && items * ((D.T + per - 1) / per) < target) per = (per + 1) / 2;
     }
@@ -620,7 +667,7 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
         while (a.per > 1 && 32ll * a.per * a.tile > 200 * 1024) a.per--;
     }
     if (D.geometry == LOC_OCTREE_3D) {
-        const size_t need = (size_t)octree_persistent_warps(D) * 10 * a.per * D.n_ch;
+        const size_t need = (size_t)octree_max_warps(D) * 10 * a.per * D.n_ch;
         if (need > m->oct_scratch_floats) {
             LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
             dev_free_all(m, m->oct_mem);
@@ -835,6 +882,8 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         cudaMemcpy(&mc, D.maser_count, sizeof(mc), cudaMemcpyDeviceToHost);
         cudaMemcpy(&uc, D.upd_count, sizeof(uc), cudaMemcpyDeviceToHost);
         r->n_maser_cells = (int64_t)mc;
+        r->path_records = m->path_records;
+        r->coll_table = D.coll_rates ? 1 : 0;
         if (prof) {
             r->march_ms = t_mar;
             r->se_ms = t_se;
@@ -1104,6 +1153,7 @@ void loc_destroy(loc_model *m)
     if (!m) return;
     cudaStreamSynchronize(m->st);
     dev_free_all(m, m->oct_mem);
+    dev_free_all(m, m->path_mem);
     dev_free_all(m, m->run_mem);
     dev_free_all(m, m->run_ab_mem);
     dev_free_all(m, m->mol_mem);

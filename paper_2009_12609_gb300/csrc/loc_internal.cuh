@@ -84,6 +84,8 @@ struct DevModel {
     int4 *oct_kids;                     // per persistent warp: child lines
     int *oct_err;                       // device flag: frame capacity exceeded
     int *oct_order;                     // root-ray families, most work first (or null)
+    unsigned long long *oct_rec;        // recorded paths of all families (or null: walk)
+    long long *oct_rec_off;             // [families + 1] first record of each family
 
     // molecule
     int L, T, P;
@@ -191,8 +193,11 @@ loc_status launch_cell_setup(const DevModel &m, const double *sigma_turb, const 
 loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream_t st);
 loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,
                                unsigned long long *count, cudaStream_t st,
-                               unsigned long long *sums = nullptr, unsigned *fam_work = nullptr);
+                               unsigned long long *sums = nullptr, unsigned *fam_work = nullptr,
+                               unsigned *fam_rec = nullptr);
+loc_status launch_record_octree(const DevModel &m, cudaStream_t st);
 int octree_persistent_warps(const DevModel &m);
+int octree_max_warps(const DevModel &m);
 loc_status launch_map_grid3d(const DevModel &m, int t, int dir, float *T_dev, cudaStream_t st);
 loc_status launch_map_octree(const DevModel &m, int t, int dir, int lam, float *T_dev, cudaStream_t st);
 constexpr int kOctMaxKids = 96;         // child lines one frame can hold

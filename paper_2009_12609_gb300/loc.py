@@ -55,7 +55,8 @@ class loc_model_desc(ctypes.Structure):
                 ("v", _d), ("vx", _d), ("vy", _d), ("vz", _d),
                 ("n_ch", ctypes.c_int), ("v_min", ctypes.c_double), ("dv", ctypes.c_double),
                 ("t_bg", ctypes.c_double), ("stream", _vp),
-                ("allocator", ctypes.POINTER(loc_allocator)), ("ray_power", ctypes.c_double)]
+                ("allocator", ctypes.POINTER(loc_allocator)), ("ray_power", ctypes.c_double),
+                ("octree_paths", ctypes.c_int)]
 
 
 class loc_molecule_desc(ctypes.Structure):
@@ -80,7 +81,8 @@ class loc_iter_report(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("n_maser_cells", ctypes.c_int64),
                 ("march_ms", ctypes.c_double), ("se_ms", ctypes.c_double),
                 ("params_ms", ctypes.c_double), ("march_launches", ctypes.c_int64),
-                ("computed_updates", ctypes.c_double)]
+                ("computed_updates", ctypes.c_double), ("path_records", ctypes.c_int64),
+                ("coll_table", ctypes.c_int)]
 
 
 class loc_server_opts(ctypes.Structure):
@@ -253,6 +255,7 @@ def model_desc(model, keep, stream=None, allocator=None):
             d.octree_levels = int(model["levels"])
             d.octree_refine = ref.ctypes.data_as(_i32)
             d.octree_n_cells = len(ref)
+            d.octree_paths = int(model.get("octree_paths", 0) or 0)
     else:
         raise ValueError(f"unknown geometry {geo}")
     d.n_ch = int(model["n_ch"])
@@ -343,7 +346,8 @@ def loc_iterate(h, **opts):
                 segments=r.segments, updates=r.updates, kernel_ms=r.kernel_ms,
                 n_maser_cells=r.n_maser_cells, march_ms=r.march_ms, se_ms=r.se_ms,
                 params_ms=r.params_ms, march_launches=r.march_launches,
-                computed_updates=r.computed_updates)
+                computed_updates=r.computed_updates, path_records=r.path_records,
+                coll_table=r.coll_table)
 
 
 def loc_autotune(h, **opts):

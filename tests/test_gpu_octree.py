@@ -185,3 +185,65 @@ def test_octree_full_size_isothermal(loc):
     S = nbg[:, None]
     Jbar = (sij + S * (norm - esc)) / norm
     np.testing.assert_allclose(Jbar / S, 1.0, rtol=3e-5)
+
+
+def test_octree_replay_equals_walk(loc, oracle):
+    """The recorded paths (default) and the tree walk in every march
+    (octree_paths = 1) apply the same steps in the same order: the
+    accumulators agree to FP32 atomic-ordering noise, and the report says
+    which one ran."""
+    mol = LI.rotor_molecule()
+    model = LI.small_octree(N=12, levels=3, refine_frac=0.15, nside=2, n_ch=24, box_pc=0.2,
+                            abundance=1e-5, seed=5)
+    out = {}
+    for paths in (0, 1):
+        with loc.Model(dict(model, octree_paths=paths), mol) as m:
+            rep = m.iterate(max_iter=1, window_sigmas=8.0, lines_per_pass=4)
+            out[paths] = (rep, m.radiation())
+    assert out[0][0]["path_records"] >= out[0][0]["segments"] > 0
+    assert out[1][0]["path_records"] == 0
+    for a, b in zip(out[0][1], out[1][1]):
+        np.testing.assert_allclose(a, b, rtol=2e-6, atol=1e-9 * np.abs(b).max())
+
+
+@pytest.fixture(scope="module")
+def bench_recipe_octree(oracle):
+    """The bench's octree recipe (refined up to 5 levels where n > 8 x mean,
+    64 channels, 48 directions, 11 lines) on a 12^3 root: 57,077 leaves.
+    Oracle: the radiation of one march at LTE and the populations after 3
+    ALI iterations."""
+    model = LI.octree_cloud(N=12)
+    mol = LI.rotor_molecule()
+    assert model["levels"] == 5
+    lm = oracle.leaf_model(model)
+    x0 = oracle.lte_populations(mol, lm["t_kin"])
+    Kp, S = oracle.line_params(mol, lm, x0)
+    rad = oracle.march_octree(mol, model, Kp, S)
+    x3, _ = oracle.iterate_octree(mol, model, 3)
+    return model, mol, rad, x3
+
+
+@pytest.mark.parametrize("per", [6, 11, 0])
+def test_octree_bench_launch_shapes(loc, oracle, bench_recipe_octree, per):
+    """Parity at the launch shapes of the bench's octree: 6 and 11 lines per
+    warp and the autotuned choice (per = 0), 8-sigma window, replayed paths."""
+    model, mol, (rs, re_, rn), x3 = bench_recipe_octree
+    with loc.Model(model, mol) as m:
+        if per == 0:
+            m.autotune(window_sigmas=8.0)
+        m.march(window_sigmas=8.0, lines_per_pass=per)
+        sij, esc, norm = m.radiation()
+        m.reset()
+        rep = m.iterate(max_iter=3, window_sigmas=8.0, lines_per_pass=per)
+        assert rep["path_records"] > 0
+        tex = [m.tex(t) for t in range(len(mol["line_nu"]))]
+    np.testing.assert_allclose(norm, rn, rtol=2e-5, atol=1e-7 * rn.max())
+    for t in range(len(mol["line_nu"])):
+        np.testing.assert_allclose(sij[t], rs[t], rtol=5e-5, atol=1e-6 * np.abs(rs[t]).max())
+        np.testing.assert_allclose(esc[t], re_[t], rtol=5e-5, atol=1e-6 * np.abs(re_[t]).max())
+    tref = oracle.tex(mol, x3)
+    for t in range(tref.shape[0]):
+        sel = x3[:, mol["line_u"][t]] >= 1e-6
+        if sel.any():
+            err = np.max(np.abs(tex[t][sel] / tref[t, sel] - 1.0))
+            assert err < 1e-4, (t, err)
