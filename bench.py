@@ -1,25 +1,29 @@
 """Benchmark of the LOC ALI hot path on GB300.
 
-Default workload: the 1D multilevel rotor cloud (256 shells, 12 levels /
-11 lines, 256 channels, seeded lognormal-perturbed power-law density, T_kin
-10-30 K), one step = one complete ALI solve from LTE (50 iterations of line
-parameters -> ray march -> statistical equilibrium) plus the emergent
-spectra of the J=1-0 line at every impact parameter.  Metric: cell-channel
-updates per second (one update = one (ray step, channel, line) application
-of the formal solution; channels skipped by the 8-sigma window count as
-updated, the computed count is reported beside it).
+Default workload: the octree cloud (64^3 root refined up to 5 levels where
+the density exceeds 8x the mean, 7.9e6 leaves, 12-level rotor / 11 lines,
+64 channels, 48 HEALPix directions), one step = one ALI iteration (line
+parameters -> ray march -> statistical equilibrium) from LTE.  Metric:
+cell-channel updates per second (one update = one (ray step, channel, line)
+application of the formal solution; channels skipped by the 8-sigma window
+count as updated, lines left out by --level-cutoff do not; the computed
+count is reported beside it).  The same JSON line carries the serving
+stream's result (--serve-requests seeded 1D models solved to 1e-4 T_ex by
+the continuous-batching server: converged models/s, p50/p99 latency, and
+the ratio over the plain per-model FP64-accumulation path).
 
-Other workloads (``--workload``): ``twolevel1d`` (32-shell two-level cloud,
-20 iterations) and ``grid3d`` (128^3 regular grid, 48 directions, 128
-channels, one ALI iteration per step).
+Other workloads (``--workload``): ``rotor1d`` (256-shell 1D rotor cloud,
+50 iterations + spectra per step), ``hotcore1d``, ``twolevel1d``,
+``grid3d`` (128^3 regular grid, one iteration per step) and ``serve``
+(the serving stream alone).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a
 bounded sample of the same workload (the only other place this script runs
 the oracle is the cpu_baseline leg).
 
-Multi-GPU: one process per GPU under torchrun; the 1D models do not shard,
-so every rank solves its own replica (weak scaling, no collective on the
-data path); the timing is the max over ranks.
+Multi-GPU: one process per GPU under torchrun; the models do not shard in
+this script, so every rank solves its own replica (weak scaling, no
+collective on the data path); the timing is the max over ranks.
 """
 import argparse
 import json
@@ -47,6 +51,7 @@ MARCH_SOURCES = {
     "march1d_runs": ["k_march.cuh", "k_march1d.cu", "loc_internal.cuh"],
     "march3d_kernel": ["k_march.cuh", "k_march3d.cu", "walk3d.cuh", "loc_internal.cuh"],
     "march_octree_kernel": ["k_march.cuh", "k_octree.cu", "loc_internal.cuh"],
+    "replay_octree_kernel": ["k_march.cuh", "k_octree.cu", "loc_internal.cuh"],
 }
 
 
@@ -123,6 +128,31 @@ def workload(name, n_root=128):
                          "48 HEALPix directions, 1 ALI iteration",
                     key="octree", mol=mol, model=model, n_iter=1, spectra=False)
     raise SystemExit(f"unknown workload {name}")
+
+
+def bytes_per_step(geometry, T, precision="fp32"):
+    """Algorithmic bytes one ray step moves: its step record (1D: cell, s,
+    v_los, w; octree: the 8-byte path record) and the cell's velocity /
+    line width, {K, S} of every line, and the read-modify-write of the
+    cell's {SIJ, ESC} per line and NORM -- plus, compensated, of their
+    compensation words (FP64 accumulation: 16 bytes per line and 8 for NORM
+    instead of 8 and 4)."""
+    rec = {"shells1d": 16 + 4, "grid3d": 16, "octree3d": 8 + 16}[geometry]
+    if precision == "fp64acc":
+        return rec + 8 * T + 2 * 16 * T + 2 * 8
+    acc = 2 * 8 * T + 2 * 4
+    if precision == "fp32":
+        acc *= 2
+    return rec + 8 * T + acc
+
+
+def bench_config(wl, args, world):
+    """The workload's config dict, the same in both arms."""
+    return {"workload": wl["name"], "iterations_per_step": wl["n_iter"],
+            "channels": wl["model"]["n_ch"], "lines": len(wl["mol"]["line_nu"]),
+            "window_sigmas": WINDOW, "models_per_step": world,
+            "level_cutoff": args.level_cutoff,
+            "parallelism": f"replicas x{world}" if world > 1 else "single"}
 
 
 # ----------------------------------------------------------------------------
@@ -262,7 +292,8 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": "cell-channel updates/s", "value": v,
             "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": {"workload": wl["name"]},
+            "data": "synthetic (seeded)",
+            "config": bench_config(wl, args, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
@@ -324,8 +355,9 @@ def run_gpu(args, wl):
     is1d = model["geometry"] == "shells1d"
     R = model["radius"][-1] if is1d else None
     p_spec = np.concatenate([[0.0], (np.arange(model["n_rays"]) + 0.5) * R / model["n_rays"]]) if is1d else None
-    opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW, level_cutoff=args.level_cutoff)
-    tune_opts = dict(window_sigmas=WINDOW, level_cutoff=args.level_cutoff)
+    opts = dict(max_iter=wl["n_iter"], window_sigmas=WINDOW, level_cutoff=args.level_cutoff,
+                precision=args.precision)
+    tune_opts = dict(window_sigmas=WINDOW, level_cutoff=args.level_cutoff, precision=args.precision)
 
     m = loc.Model(model, mol)
     stream = torch.cuda.current_stream()
@@ -375,8 +407,11 @@ def run_gpu(args, wl):
 
     seg = reps[0]["segments"]
     iters = reps[0]["iterations"]
-    upd_step = seg * nch * T * iters                    # nominal updates per step
-    value = replicas_throughput(upd_step * args.steps, world, ms_total / 1e3)
+    # nominal updates: every channel of every (step, line) that is not left
+    # out by the per-cell line truncation, counted on the device
+    nominal = sum(r["nominal_updates"] for r in reps)
+    upd_step = nominal / args.steps
+    value = replicas_throughput(nominal, world, ms_total / 1e3)
 
     # dominant kernel: the ray march (CUDA events around every launch, on the
     # launching stream, inside loc_iterate)
@@ -391,17 +426,20 @@ def run_gpu(args, wl):
     # ALU roofline: 10 FP32-pipe operations per computed update at 128 lanes/SM
     alu_peak = n_sm * 128 * sm_max * 1e6 / 10.0 / 1e9            # Gupd/s
     achieved = comp / launches / per_launch_s / 1e9               # computed Gupd/s
-    bytes_per_seg = 28 + 24 * T
+    bytes_per_seg = bytes_per_step(model["geometry"], T, args.precision)
     hbm_achieved = seg * bytes_per_seg / per_launch_s / 1e9       # algorithmic GB/s
     # 1D rays cut into runs: the march is the affine + scan + run launches
     runs = is1d and tuned_chunk > 0
+    replay = model["geometry"] == "octree3d" and reps[0]["path_records"] > 0
     kernel = ("march1d_runs" if runs else "march1d_kernel") if is1d else (
-        "march_octree_kernel" if model["geometry"] == "octree3d" else "march3d_kernel")
+        ("replay_octree_kernel" if replay else "march_octree_kernel")
+        if model["geometry"] == "octree3d" else "march3d_kernel")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupd/s",
                 "frac": achieved / alu_peak,
                 "traffic": committed_traffic(kernel, wl["key"]),
                 "traffic_unit": "DRAM bytes per launch (ncu, cold cache)",
                 "algorithmic_bytes_per_launch": seg * bytes_per_seg,
+                "algorithmic_bytes_per_step": bytes_per_seg,
                 "kernel": kernel,
                 "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / 10 ops per update",
                 "hbm_algorithmic_gbs": hbm_achieved,
@@ -443,6 +481,10 @@ def run_gpu(args, wl):
     per_iter_launches = 4 if runs else 2
     gpu_launches = args.steps * (iters * per_iter_launches + 1 + (4 if wl["spectra"] else 1))
 
+    m.close()
+    serving = None
+    if world == 1 and args.serve_requests > 0:
+        serving = serve_measure(args, args.serve_requests)
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -453,14 +495,18 @@ def run_gpu(args, wl):
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-                "config": {"workload": wl["name"], "iterations_per_step": iters,
-                           "ray_steps_per_iteration": seg, "channels": nch, "lines": T,
-                           "window_sigmas": WINDOW, "models_per_step": world,
-                           "level_cutoff": args.level_cutoff,
-                           "lines_per_warp": tuned_per,
-                           "steps_per_chunk": tuned_chunk,
-                           "parallelism": f"replicas x{world}" if world > 1 else "single",
-                           "l2": "flushed (256 MB write) between timed steps"},
+                "config": bench_config(wl, args, world),
+                "precision": {"fp32": "FP32 march, compensated FP32 accumulation",
+                              "fp32plain": "FP32 march, plain FP32 accumulation",
+                              "fp64acc": "FP32 march, FP64 accumulation"}[args.precision],
+                "launch": {"lines_per_warp": tuned_per, "steps_per_chunk": tuned_chunk,
+                           "march_kernel": kernel},
+                "work": {"ray_steps_per_iteration": seg, "octree_path_records": reps[0]["path_records"],
+                         "collision_rate_table": bool(reps[0]["coll_table"]),
+                         "nominal_updates_per_step": upd_step,
+                         "computed_updates_per_step": comp / args.steps},
+                "timing": {"l2": "flushed (256 MB write) between timed steps",
+                           "clock": "CUDA events on the model's stream"},
                 "computed_updates_per_s": replicas_throughput(comp, world, ms_total / 1e3),
                 "models_per_s": world * 1e3 / ms_step,
                 "kernel_ms_per_step": {"march": march_ms / args.steps, "se": se_ms / args.steps,
@@ -471,24 +517,24 @@ def run_gpu(args, wl):
                         "seconds_per_step": split},
                 "gpu_launches": gpu_launches, "clocks": clocks,
                 "wall_s_timed": wall, "peak_source": peak_src}
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line))
-    m.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_serve(args):
-    """Continuous-batching server on the stream of seeded 1D requests:
+def serve_measure(args, n):
+    """Continuous-batching server on the stream of n seeded 1D requests:
     closed loop (all submitted at once) for the saturated converged-models/s,
     then Poisson arrivals at 0.8x that rate for p50/p99 latency; beside it the
-    plain path: the same requests solved one at a time with FP64 per-cell
-    accumulation."""
+    plain path: the first requests of the stream solved one at a time with
+    FP64 per-cell accumulation, and the server on that same set."""
     import torch
     from paper_2009_12609_gb300 import build, loc
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     build.build()
     loc.load()
-    n = args.requests
     tol, max_iter = 1e-4, 300
     cut = args.level_cutoff
     reqs = LI.serving_requests(n=n)
@@ -510,7 +556,7 @@ def run_serve(args):
     clocks = clk.stop()
     conv = sum(1 for r in res if r["status"] == 0)
     upd = sum(r["updates"] for r in res)
-    models_per_s = n / closed_s
+    models_per_s = conv / closed_s          # converged models only
     # open loop: Poisson arrivals at 0.8x the saturated rate
     rate = 0.8 * models_per_s
     n_open = min(n, args.open_requests)
@@ -530,28 +576,27 @@ def run_serve(args):
     n_base = min(n, args.baseline_requests)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    base_conv = 0
     for r in reqs[:n_base]:
         with loc.Model(r["model"], mols[r["n_levels"]]) as m:
-            m.iterate(max_iter=max_iter, tol_tex=tol, precision="fp64acc", window_sigmas=WINDOW,
-                      level_cutoff=cut)
+            rep = m.iterate(max_iter=max_iter, tol_tex=tol, precision="fp64acc", window_sigmas=WINDOW,
+                            level_cutoff=cut)
+            base_conv += rep["status"] == 0
     torch.cuda.synchronize()
-    base_models_per_s = n_base / (time.perf_counter() - t0)
+    base_models_per_s = base_conv / (time.perf_counter() - t0)
     with loc.Server(**srv_opts) as srv:
         t0 = time.perf_counter()
         ts = [srv.submit(r["model"], mols[r["n_levels"]], max_iter=max_iter, tol_tex=tol, level_cutoff=cut)
               for r in reqs[:n_base]]
-        for t in ts:
-            srv.poll(t, 3600 * 1000)
-        same_set_models_per_s = n_base / (time.perf_counter() - t0)
-    line = {"metric": "converged 1D models/s at 1e-4 T_ex", "value": models_per_s,
-            "unit": "models/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded)",
-            "config": {"workload": f"serving stream: {n} seeded 1D requests, shells U(32..1024), "
-                                   "channels {64,128,256,512}, levels U(2..20), scales x[0.1,10]",
-                       "slots": args.slots, "iters_per_launch": 4, "window_sigmas": WINDOW,
-                       "tol_tex": tol, "max_iter": max_iter, "level_cutoff": cut},
-            "converged": conv, "updates_per_s": upd / closed_s,
+        same_conv = sum(1 for t in ts if srv.poll(t, 3600 * 1000)[0]["status"] == 0)
+        same_set_models_per_s = same_conv / (time.perf_counter() - t0)
+    return {"metric": "converged 1D models/s at 1e-4 T_ex", "value": models_per_s, "unit": "models/s",
+            "workload": f"serving stream: {n} seeded 1D requests, shells U(32..1024), "
+                        "channels {64,128,256,512}, levels U(2..20), scales x[0.1,10]",
+            "requests": n, "converged": conv, "closed_loop_s": closed_s,
+            "slots": args.slots, "iters_per_launch": 4, "window_sigmas": WINDOW,
+            "tol_tex": tol, "max_iter": max_iter, "level_cutoff": cut,
+            "updates_per_s": upd / closed_s,
             "latency_open_loop": {"rate_hz": rate, "requests": n_open,
                                   "p50_ms": float(np.percentile(lat, 50)),
                                   "p99_ms": float(np.percentile(lat, 99)),
@@ -561,6 +606,18 @@ def run_serve(args):
             "same_requests": n_base,
             "speedup_vs_per_model_fp64acc": same_set_models_per_s / base_models_per_s,
             "clocks": clocks}
+
+
+def run_serve(args):
+    """--workload serve: the serving stream alone, as its own JSON line."""
+    r = serve_measure(args, args.requests)
+    line = {"metric": r["metric"], "value": r["value"], "unit": r["unit"], "n_gpus": 1,
+            "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": r["workload"], "slots": r["slots"],
+                       "iters_per_launch": r["iters_per_launch"], "window_sigmas": WINDOW,
+                       "tol_tex": r["tol_tex"], "max_iter": r["max_iter"], "level_cutoff": r["level_cutoff"]},
+            **{k: v for k, v in r.items() if k not in ("metric", "value", "unit", "workload")}}
     print(json.dumps(line))
 
 
@@ -570,9 +627,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rotor1d",
+    ap.add_argument("--workload", default="octree",
                     choices=["rotor1d", "hotcore1d", "twolevel1d", "grid3d", "octree", "serve"])
-    ap.add_argument("--requests", type=int, default=512, help="serve: requests in the stream")
+    ap.add_argument("--requests", type=int, default=4096, help="serve: requests in the stream")
+    ap.add_argument("--serve-requests", type=int, default=-1,
+                    help="requests of the serving stream measured after the main workload and "
+                         "reported in the same line (default: 4096 for the octree workload, "
+                         "0 otherwise; 0 skips it)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32plain", "fp64acc"],
+                    help="accumulation of the march: compensated FP32 (default), plain FP32, FP64")
     ap.add_argument("--open-requests", type=int, default=256, help="serve: open-loop requests")
     ap.add_argument("--baseline-requests", type=int, default=256,
                     help="serve: requests solved one at a time by the per-model FP64 path")
@@ -590,6 +653,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
+    if args.serve_requests < 0:
+        args.serve_requests = 4096 if args.workload == "octree" else 0
     if args.workload == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serve workload has no CPU arm"}))

@@ -49,9 +49,16 @@ typedef int loc_status;
 #define LOC_GRID_3D   2
 #define LOC_OCTREE_3D 3
 
-/* Accumulation precision of the ray march. */
-#define LOC_FP32_MARCH 0  /* FP32 march and FP32 per-cell accumulators      */
+/* Accumulation precision of the ray march (Eq. 2: the per-cell sums of
+ * absorbed photons and escape terms over all ray steps). */
+#define LOC_FP32_MARCH 0  /* FP32 march; FP32 per-cell accumulators whose
+                             additions are compensated: the exact rounding
+                             error of every atomic addition (TwoSum on the
+                             value it found) goes to a second FP32 word, and
+                             the solve reads the sum of both (the default) */
 #define LOC_FP64_ACC   1  /* FP32 march, FP64 per-cell accumulators         */
+#define LOC_FP32_PLAIN 2  /* FP32 march, plain FP32 accumulators (no
+                             compensation; for error comparisons)           */
 
 /* Optional device allocator; alloc returns NULL on failure. */
 typedef struct loc_allocator {
@@ -157,7 +164,7 @@ typedef struct loc_molecule_desc {
  *                 whose upper level holds >= 1e-6 of the molecules.
  *  ali            1: accelerated lambda iteration with the diagonal
  *                 operator (Sect. 2); 0: plain lambda iteration.
- *  precision      LOC_FP32_MARCH or LOC_FP64_ACC.
+ *  precision      LOC_FP32_MARCH (default), LOC_FP64_ACC or LOC_FP32_PLAIN.
  *  lines_per_pass 0: automatic (the value chosen by loc_autotune, else all
  *                 lines per warp, or fewer when the launch would leave
  *                 SMs idle); k > 0: each warp carries k lines through the
@@ -215,6 +222,8 @@ typedef struct loc_iter_report {
     double params_ms;          /* summed duration of the line-parameter step*/
     int64_t march_launches;    /* number of march launches                  */
     double computed_updates;   /* updates inside the channel windows        */
+    double nominal_updates;    /* updates of every channel of every line not
+                                  left out by level_cutoff in the step's cell */
     /* how the work was done (always filled) */
     int64_t path_records;      /* octree: recorded path records the march
                                   replays (0: it walks the tree)             */

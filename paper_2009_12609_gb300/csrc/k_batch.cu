@@ -30,8 +30,7 @@ __global__ void batch_clear_kernel(BatchSlot *slots, int n_slots)
     if (s >= n_slots || !slots[s].active) return;
     const DevModel &m = slots[s].m;
     const long long n = (long long)m.n_cells * m.T;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) m.acc[i] = make_float2(0.f, 0.f);
-    for (long long i = threadIdx.x; i < m.n_cells; i += blockDim.x) m.norm[i] = 0.f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) acc_zero(m, i, i / m.T, 0, (i % m.T) == 0);
 }
 
 __global__ void batch_params_kernel(BatchSlot *slots, int n_slots)
@@ -69,9 +68,10 @@ batch_march_kernel(BatchSlot *slots, const int4 *items, const int *n_items, unsi
         a0.window = window;
         a0.inv_dv = S->inv_dv;
         a0.fp64_acc = 0;
+        a0.comp = m.acc_c != nullptr;
         a0.count = 0;
         const MarchArgs a = warp_args(m, a0, w.z);
-        march_ray1d<G>(m, a, I, w.y, lane);
+        march_ray1d<G, kAccComp>(m, a, I, w.y, lane);
         __syncwarp();
     }
 }

@@ -17,9 +17,13 @@
 // of the group, channels optionally restricted to a window around the local
 // line centre (Sect. A.2).  The per-step sums {SIJ_t, ESC_t, NORM} of all
 // lanes are combined by a transpose-reduction that leaves line t's totals
-// in lane t, so each step ends with one coalesced vector atomic {SIJ, ESC}
-// per line into the cell's contiguous [cell][line] record.  The next step's
-// cell data is loaded while the current step computes.
+// in lane t, so each step ends with one
+// coalesced vector atomic {SIJ, ESC} per line into the cell's contiguous
+// [cell][line] record.  The FP32 atomics are compensated: each lane keeps
+// the value its last atomic found and, one step later (when it has long
+// arrived), adds the exact rounding error of that addition (TwoSum) to a
+// compensation word of the same element.  The next step's cell data is
+// loaded while the current step computes.
 #pragma once
 
 #include "loc_internal.cuh"
@@ -29,6 +33,46 @@ namespace loc {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr unsigned kFull = 0xffffffffu;
+
+// Accumulation of the per-cell sums, fixed when a march kernel is compiled:
+// plain FP32 atomics, compensated FP32 atomics, or FP64 atomics.
+constexpr int kAccPlain = 0, kAccComp = 1, kAccF64 = 2;
+
+inline int acc_mode(const MarchArgs &a) { return a.fp64_acc ? kAccF64 : (a.comp ? kAccComp : kAccPlain); }
+
+// Register-array sizes (lines per warp) the march kernels are compiled for:
+// a group of `per` lines runs in the smallest of them >= per.
+__host__ __device__ constexpr int march_g(int per)
+{
+    return per <= 4 ? per : per <= 6 ? 6 : per <= 8 ? 8 : per <= 11 ? 11 : 15;
+}
+
+// f.template go<G, ACC>() for the compiled G of a.per and a's accumulation
+template <int G, class F>
+loc_status march_dispatch_acc(int mode, const F &f)
+{
+    switch (mode) {
+    case kAccComp: return f.template go<G, kAccComp>();
+    case kAccF64: return f.template go<G, kAccF64>();
+    default: return f.template go<G, kAccPlain>();
+    }
+}
+
+template <class F>
+loc_status march_dispatch(const MarchArgs &a, const F &f)
+{
+    const int mode = acc_mode(a);
+    switch (march_g(a.per)) {
+    case 1: return march_dispatch_acc<1>(mode, f);
+    case 2: return march_dispatch_acc<2>(mode, f);
+    case 3: return march_dispatch_acc<3>(mode, f);
+    case 4: return march_dispatch_acc<4>(mode, f);
+    case 6: return march_dispatch_acc<6>(mode, f);
+    case 8: return march_dispatch_acc<8>(mode, f);
+    case 11: return march_dispatch_acc<11>(mode, f);
+    default: return march_dispatch_acc<15>(mode, f);
+    }
+}
 
 // Channel fraction of a Gaussian between b0 and b0 + db (arguments in units
 // of sqrt(2) sigma), written with upper tails so both wings keep relative
@@ -68,6 +112,59 @@ __device__ __forceinline__ float warp_sum(float v)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
     return v;
+}
+
+// Exact rounding error of the FP32 sum a + b (Knuth's TwoSum): with s the
+// rounded sum, a + b = s + err exactly.  Explicit round-to-nearest
+// operations keep the compiler from contracting or reordering them.
+__device__ __forceinline__ float two_sum_err(float a, float b)
+{
+    const float sum = __fadd_rn(a, b);
+    const float bb = __fsub_rn(sum, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+}
+
+// State a lane carries from step to step of one ray: its last compensated
+// atomic -- the element, the value added and the value the atomic found
+// there (the atomic rounds old + v to nearest, so two_sum_err(old, v) is
+// exactly what the stored sum lacks) -- and, when counting, the (step, line)
+// pairs of the steps so far whose line is not truncated in the step's cell
+// (each stands for n_ch nominal channel updates).
+struct MarchState {
+    float2 old, v;
+    long long o;
+    int kind;               // 0 none, 1 {SIJ, ESC} of element o, 2 NORM of cell o
+    long long nom;
+};
+
+__device__ __forceinline__ void acc_flush(const DevModel &m, MarchState &p)
+{
+    if (p.kind == 1)
+        atomicAdd(m.acc_c + p.o, make_float2(two_sum_err(p.old.x, p.v.x), two_sum_err(p.old.y, p.v.y)));
+    else if (p.kind == 2)
+        atomicAdd(m.norm_c + p.o, two_sum_err(p.old.x, p.v.x));
+    p.kind = 0;
+}
+
+__device__ __forceinline__ MarchState march_state()
+{
+    MarchState p;
+    p.old = make_float2(0.f, 0.f);
+    p.v = make_float2(0.f, 0.f);
+    p.o = 0;
+    p.kind = 0;
+    p.nom = 0;
+    return p;
+}
+
+// end of a ray: the pending compensation, and the nominal count (profiling;
+// p.nom counts (step, line) pairs, each worth n_ch channel updates)
+template <int ACC>
+__device__ __forceinline__ void march_state_end(const DevModel &m, const MarchArgs &a, MarchState &p, int lane)
+{
+    if constexpr (ACC == kAccComp) acc_flush(m, p);
+    if (a.count && lane == 0 && p.nom) atomicAdd(m.nom_count, (unsigned long long)p.nom * (unsigned long long)m.n_ch);
+    p.nom = 0;
 }
 
 // Sum of v[i] over the 32 lanes for all i at once; lane l receives the
@@ -149,16 +246,70 @@ __device__ __forceinline__ bool lines_off(const DevModel &m, const MarchArgs &a,
     return off;
 }
 
+// Lane of a warp that adds the step's NORM (lanes t < n_lines <= G add the
+// lines' {SIJ, ESC}); the transpose reduction leaves NORM in lane 15.
+template <int G>
+__device__ __forceinline__ constexpr int norm_lane() { return G <= 2 ? 2 * G : 15; }
+
+// Adds one step's totals to the cell: lane t < n_lines holds line t's
+// channel sums {sum I t_k, sum t_k} (t_k = 1 - e^-tau_k), which become
+// {SIJ, ESC} with the factor w / ks (ks = line t's K s, step_ks); lane
+// norm_lane<G>() holds sum phi_k.
+// Compensated FP32: the previous atomic of the lane gets its rounding error
+// added first (its result has arrived by now), then the new one is issued
+// and remembered.
+template <int G, int ACC>
+__device__ __forceinline__ void step_commit(const DevModel &m, const MarchArgs &a, long long cell, float ks,
+                                            float w, int lane, float my_sij, float my_esc, float my_nrm,
+                                            MarchState &pend)
+{
+    if (lane < a.n_lines) {
+        const long long o = cell * m.T + a.line0 + lane;
+        if constexpr (ACC == kAccF64) {
+            const double f = (double)w / (double)ks;
+            atomicAdd(m.acc64 + 2 * o, f * (double)my_sij);
+            atomicAdd(m.acc64 + 2 * o + 1, f * (double)my_esc);
+        } else {
+            const float f = __fdividef(w, ks);
+            const float2 v = make_float2(my_sij * f, my_esc * f);
+            if constexpr (ACC == kAccPlain) {
+                atomicAdd(m.acc + o, v);
+            } else {
+                acc_flush(m, pend);
+                pend.old = atomicAdd(m.acc + o, v);
+                pend.v = v;
+                pend.o = o;
+                pend.kind = 1;
+            }
+        }
+    } else if (a.do_norm && lane == norm_lane<G>()) {
+        if constexpr (ACC == kAccF64) {
+            atomicAdd(m.norm64 + cell, (double)w * (double)my_nrm);
+        } else {
+            const float v = w * my_nrm;
+            if constexpr (ACC == kAccPlain) {
+                atomicAdd(m.norm + cell, v);
+            } else {
+                acc_flush(m, pend);
+                pend.old = make_float2(atomicAdd(m.norm + cell, v), 0.f);
+                pend.v = make_float2(v, 0.f);
+                pend.o = cell;
+                pend.kind = 2;
+            }
+        }
+    }
+}
+
 // Narrow windows (at most 16 channels): the lanes take (line, channel) pairs,
 // 32 / Wp lines per chunk with Wp the window rounded up to a power of two.
 // The profile is evaluated once per step (lane c holds channel klo + c), the
 // line parameters come from the lane that holds them, and a segmented
-// reduction over each Wp-lane segment leaves line t's sums in the segment's
-// first lane, which adds them to the cell.
-template <int G>
+// reduction over each Wp-lane segment gives every lane of the segment line
+// t's sums; lane t collects them for step_commit.
+template <int G, int ACC>
 __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchArgs &a, float *I,
                                                  const Step<G> &st, int lane, int klo, int khi,
-                                                 float u0, float db)
+                                                 float u0, float db, MarchState &pend)
 {
     const int W = khi - klo;
     if (W <= 0) return 0;
@@ -184,6 +335,7 @@ __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchA
         }
     }
     const int tl = lane / Wp, kk = lane - tl * Wp;
+    float g_sij = 0.f, g_esc = 0.f;
     for (int base = 0; base < a.n_lines; base += P) {
         const int t = base + tl;
         const bool act = (kk < W) && (t < a.n_lines);
@@ -203,40 +355,43 @@ __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchA
             ps += __shfl_xor_sync(kFull, ps, off);
             pe += __shfl_xor_sync(kFull, pe, off);
         }
-        if (kk == 0 && t < a.n_lines) {
-            const long long o = st.cell * m.T + a.line0 + t;
-            if (a.fp64_acc) {
-                const double f = (double)st.w / (double)Kt;
-                atomicAdd(m.acc64 + 2 * o, f * (double)ps);
-                atomicAdd(m.acc64 + 2 * o + 1, f * (double)pe);
-            } else {
-                const float f = __fdividef(st.w, Kt);
-                atomicAdd(m.acc + o, make_float2(ps * f, pe * f));
-            }
+        // line base + j's sums sit in segment j: lane base + j takes them
+        const int j = lane - base;
+        const int src = (j >= 0 && j < P) ? j * Wp : 0;
+        const float vs = __shfl_sync(kFull, ps, src), ve = __shfl_sync(kFull, pe, src);
+        if (j >= 0 && j < P) {
+            g_sij = vs;
+            g_esc = ve;
         }
     }
-    if (a.do_norm) {
-        const float nrm = warp_sum(phi_c);
-        if (lane == 0) {
-            if (a.fp64_acc) atomicAdd(m.norm64 + st.cell, (double)st.w * (double)nrm);
-            else atomicAdd(m.norm + st.cell, st.w * nrm);
-        }
-    }
+    const float nrm = a.do_norm ? warp_sum(phi_c) : 0.f;
+    step_commit<G, ACC>(m, a, st.cell, my_k, st.w, lane, g_sij, g_esc, nrm, pend);
     return W;
 }
 
 // Process one step.  All lanes call it with identical arguments.  Returns
-// the number of channels computed (0 for a skipped step).
-template <int G>
+// the number of channels computed (0 for a skipped step).  pend carries the
+// lane's last compensated atomic from step to step (acc_flush after the
+// last step).
+template <int G, int ACC>
 __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
-                                          const Step<G> &st, int lane)
+                                          const Step<G> &st, int lane, MarchState &pend)
 {
     if (lines_off<G>(m, a, st)) return 0;
     const int nch = m.n_ch;
+    if (a.count) {
+        int on = a.n_lines;
+        if (m.trunc) {
+            on = 0;
+#pragma unroll
+            for (int t = 0; t < G; t++) on += (t < a.n_lines) & (__float_as_uint(st.ks[t].x) != 0x80000000u);
+        }
+        pend.nom += on;
+    }
     float u0, db;
     int klo, khi;
     step_window(m, a, st, u0, db, klo, khi);
-    if (khi - klo <= 16) return march_step_packed<G>(m, a, I, st, lane, klo, khi, u0, db);
+    if (khi - klo <= 16) return march_step_packed<G, ACC>(m, a, I, st, lane, klo, khi, u0, db, pend);
     float Ks[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
@@ -294,11 +449,9 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
     } else {
         for (int base = klo; base < khi; base += 31) chunk(base);
     }
-    // lane t < n_lines ends with line t's {SIJ, ESC}; lane 15 with NORM
-    float my_sij, my_esc, my_nrm;
-    if (G <= 2) {
-        my_sij = 0.f;
-        my_esc = 0.f;
+    // lane t < n_lines ends with line t's {SIJ, ESC}; norm_lane<G>() with NORM
+    float my_sij = 0.f, my_esc = 0.f, my_nrm = 0.f;
+    if constexpr (G <= 2) {
 #pragma unroll
         for (int t = 0; t < G; t++) {
             const float a1 = warp_sum(sij[t]), a2 = warp_sum(esc[t]);
@@ -306,6 +459,7 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
         }
         my_nrm = a.do_norm ? warp_sum(nrm) : 0.f;
     } else {
+        // SIJ of line t in value t, ESC in 16 + t, NORM in 15 (= norm_lane)
         float v[32];
 #pragma unroll
         for (int i = 0; i < 32; i++) v[i] = 0.f;
@@ -315,26 +469,12 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
         const float r = transpose_reduce32(v, lane);
         my_sij = r;
         my_esc = __shfl_down_sync(kFull, r, 16);
-        my_nrm = r;   // meaningful in lane 15
+        my_nrm = r;
     }
-    if (a.do_norm && lane == 15) {
-        if (a.fp64_acc) atomicAdd(m.norm64 + st.cell, (double)st.w * (double)my_nrm);
-        else atomicAdd(m.norm + st.cell, st.w * my_nrm);
-    }
-    if (lane < a.n_lines) {
-        float my_ks = 1.f;
+    float my_ks = 1.f;
 #pragma unroll
-        for (int t = 0; t < G; t++) if (lane == t) my_ks = Ks[t];
-        const long long o = st.cell * m.T + a.line0 + lane;
-        if (a.fp64_acc) {
-            const double f = (double)st.w / (double)my_ks;
-            atomicAdd(m.acc64 + 2 * o, f * (double)my_sij);
-            atomicAdd(m.acc64 + 2 * o + 1, f * (double)my_esc);
-        } else {
-            const float f = __fdividef(st.w, my_ks);
-            atomicAdd(m.acc + o, make_float2(my_sij * f, my_esc * f));
-        }
-    }
+    for (int t = 0; t < G; t++) if (lane == t) my_ks = Ks[t];
+    step_commit<G, ACC>(m, a, st.cell, my_ks, st.w, lane, my_sij, my_esc, my_nrm, pend);
     return khi - klo;
 }
 
@@ -402,14 +542,18 @@ __device__ __forceinline__ long long walk_steps1d(const DevModel &m, const March
 
 // One 1D ray (equidistant ray j) through all its steps for the warp's line
 // group.  Returns the number of channels computed.
-template <int G>
+template <int G, int ACC>
 __device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchArgs &a, float *I,
                                                  int j, int lane)
 {
     init_ray<G>(m, a, I, lane);
     const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
-    return walk_steps1d<G>(m, a, s0, n, lane,
-                           [&](const Step<G> &st) { return (long long)march_step<G>(m, a, I, st, lane); });
+    MarchState pend = march_state();
+    const long long nw = walk_steps1d<G>(m, a, s0, n, lane, [&](const Step<G> &st) {
+        return (long long)march_step<G, ACC>(m, a, I, st, lane, pend);
+    });
+    march_state_end<ACC>(m, a, pend, lane);
+    return nw;
 }
 
 // Eq. 3 on a step without accumulation, applied to the affine map of a run

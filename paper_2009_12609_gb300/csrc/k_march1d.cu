@@ -4,7 +4,7 @@
 
 namespace loc {
 
-template <int G>
+template <int G, int ACC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
@@ -15,42 +15,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m
     const int j = (int)(item / a0.n_groups);
     const MarchArgs a = warp_args(m, a0, (int)(item - (long long)j * a0.n_groups));
     float *I = smem + (size_t)wid * a.per * m.n_ch;
-    const long long nw = march_ray1d<G>(m, a, I, j, lane);
+    const long long nw = march_ray1d<G, ACC>(m, a, I, j, lane);
     flush_count(m, a, nw, lane);
 }
 
-// instantiate every group size 1..15 so no predicated-off line is issued
-template <int G>
-static loc_status launch_g(const DevModel &m, const MarchArgs &a, cudaStream_t st)
-{
-    const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
-    const long long items = (long long)m.n_rays * a.n_groups;
-    const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    march1d_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
-    LOC_CUDA_TRY(cudaGetLastError());
-    return LOC_OK;
-}
+struct Launch1D {
+    const DevModel &m;
+    const MarchArgs &a;
+    cudaStream_t st;
+    template <int G, int ACC>
+    loc_status go() const
+    {
+        const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+        const long long items = (long long)m.n_rays * a.n_groups;
+        const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_kernel<G, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        march1d_kernel<G, ACC><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
+        LOC_CUDA_TRY(cudaGetLastError());
+        return LOC_OK;
+    }
+};
 
 loc_status launch_march1d(const DevModel &m, const MarchArgs &a, cudaStream_t st)
 {
-    switch (a.per) {
-    case 1: return launch_g<1>(m, a, st);
-    case 2: return launch_g<2>(m, a, st);
-    case 3: return launch_g<3>(m, a, st);
-    case 4: return launch_g<4>(m, a, st);
-    case 5: return launch_g<5>(m, a, st);
-    case 6: return launch_g<6>(m, a, st);
-    case 7: return launch_g<7>(m, a, st);
-    case 8: return launch_g<8>(m, a, st);
-    case 9: return launch_g<9>(m, a, st);
-    case 10: return launch_g<10>(m, a, st);
-    case 11: return launch_g<11>(m, a, st);
-    case 12: return launch_g<12>(m, a, st);
-    case 13: return launch_g<13>(m, a, st);
-    case 14: return launch_g<14>(m, a, st);
-    default: return launch_g<15>(m, a, st);
-    }
+    return march_dispatch(a, Launch1D{m, a, st});
 }
 
 // ----------------------------------------------------------------------------
@@ -142,7 +130,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_affine_kernel(Dev
     // channel tiles of the union: each tile composes its own channels' maps
     for (int tlo = rng.x; tlo < rng.y; tlo += tile) {
         const int thi = min(rng.y, tlo + tile), w = thi - tlo;
-        for (int i = lane; i < G * w; i += 32) {
+        for (int i = lane; i < a.per * w; i += 32) {       // the tiles hold a.per <= G lines
             const int t = i / w;
             A[t * tile + i - t * w] = 1.f;
             B[t * tile + i - t * w] = 0.f;
@@ -200,8 +188,9 @@ __global__ void march1d_scan_kernel(DevModel m, MarchArgs a)
     }
 }
 
-template <int G>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_run_kernel(DevModel m, MarchArgs a0)
+// registers capped at 128 (4 blocks per SM) up to 11 lines per warp
+template <int G, int ACC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 11 ? 4 : 3) march1d_run_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
@@ -227,50 +216,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_run_kernel(DevMod
         I[t * nch + rng.x + k] = in[(size_t)t * nch + k].x;
     }
     __syncwarp();
+    MarchState pend = march_state();
     const long long nw = walk_steps1d<G>(m, a, m.ray_off[j] + q0, len, lane, [&](const Step<G> &st) {
-        return (long long)march_step<G>(m, a, I, st, lane);
+        return (long long)march_step<G, ACC>(m, a, I, st, lane, pend);
     });
+    march_state_end<ACC>(m, a, pend, lane);
     flush_count(m, a, nw, lane);
 }
 
-template <int G>
-static loc_status launch_chunked_g(const DevModel &m, const MarchArgs &a, cudaStream_t st)
-{
-    const long long items = a.n_chunks * a.n_groups;
-    const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const size_t smem_a = (size_t)kWarpsPerBlock * 2 * a.per * a.tile * sizeof(float);
-    const size_t smem_r = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
-    LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_affine_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
-    LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_run_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
-    march1d_affine_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem_a, st>>>(m, a);
-    LOC_CUDA_TRY(cudaGetLastError());
-    const long long ns = (long long)m.n_rays * m.T * m.n_ch;
-    march1d_scan_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(m, a);
-    LOC_CUDA_TRY(cudaGetLastError());
-    march1d_run_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem_r, st>>>(m, a);
-    LOC_CUDA_TRY(cudaGetLastError());
-    return LOC_OK;
-}
+struct Launch1DRuns {
+    const DevModel &m;
+    const MarchArgs &a;
+    cudaStream_t st;
+    template <int G, int ACC>
+    loc_status go() const
+    {
+        const long long items = a.n_chunks * a.n_groups;
+        const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const size_t smem_a = (size_t)kWarpsPerBlock * 2 * a.per * a.tile * sizeof(float);
+        const size_t smem_r = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+        LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_affine_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+        LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_run_kernel<G, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
+        march1d_affine_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem_a, st>>>(m, a);
+        LOC_CUDA_TRY(cudaGetLastError());
+        const long long ns = (long long)m.n_rays * m.T * m.n_ch;
+        march1d_scan_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(m, a);
+        LOC_CUDA_TRY(cudaGetLastError());
+        march1d_run_kernel<G, ACC><<<(unsigned)nb, kWarpsPerBlock * 32, smem_r, st>>>(m, a);
+        LOC_CUDA_TRY(cudaGetLastError());
+        return LOC_OK;
+    }
+};
 
 loc_status launch_march1d_chunked(const DevModel &m, const MarchArgs &a, cudaStream_t st)
 {
-    switch (a.per) {
-    case 1: return launch_chunked_g<1>(m, a, st);
-    case 2: return launch_chunked_g<2>(m, a, st);
-    case 3: return launch_chunked_g<3>(m, a, st);
-    case 4: return launch_chunked_g<4>(m, a, st);
-    case 5: return launch_chunked_g<5>(m, a, st);
-    case 6: return launch_chunked_g<6>(m, a, st);
-    case 7: return launch_chunked_g<7>(m, a, st);
-    case 8: return launch_chunked_g<8>(m, a, st);
-    case 9: return launch_chunked_g<9>(m, a, st);
-    case 10: return launch_chunked_g<10>(m, a, st);
-    case 11: return launch_chunked_g<11>(m, a, st);
-    case 12: return launch_chunked_g<12>(m, a, st);
-    case 13: return launch_chunked_g<13>(m, a, st);
-    case 14: return launch_chunked_g<14>(m, a, st);
-    default: return launch_chunked_g<15>(m, a, st);
-    }
+    return march_dispatch(a, Launch1DRuns{m, a, st});
 }
 
 // ----------------------------------------------------------------------------

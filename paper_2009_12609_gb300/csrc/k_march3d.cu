@@ -5,7 +5,7 @@
 namespace loc {
 
 // 3D regular grid: one warp per (direction, root line, line group).
-template <int G>
+template <int G, int ACC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
@@ -37,50 +37,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m
     };
     long long nw = 0;
     Step<G> cur, nxt;
+    MarchState pend = march_state();
     fetch(cur);
     while (true) {
         const bool more = !wk.done(m.N);
         if (more) fetch(nxt);
-        nw += march_step<G>(m, a, I, cur, lane);
+        nw += march_step<G, ACC>(m, a, I, cur, lane, pend);
         __syncwarp();
         if (!more) break;
         cur = nxt;
     }
+    march_state_end<ACC>(m, a, pend, lane);
     flush_count(m, a, nw, lane);
 }
 
 
-template <int G>
-static loc_status launch_g(const DevModel &m, const MarchArgs &a, cudaStream_t st)
-{
-    const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
-    const long long items = (long long)m.N * m.N * m.n_dir * a.n_groups;
-    const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    LOC_CUDA_TRY(cudaFuncSetAttribute(march3d_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    march3d_kernel<G><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
-    LOC_CUDA_TRY(cudaGetLastError());
-    return LOC_OK;
-}
+struct Launch3D {
+    const DevModel &m;
+    const MarchArgs &a;
+    cudaStream_t st;
+    template <int G, int ACC>
+    loc_status go() const
+    {
+        const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+        const long long items = (long long)m.N * m.N * m.n_dir * a.n_groups;
+        const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        LOC_CUDA_TRY(cudaFuncSetAttribute(march3d_kernel<G, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        march3d_kernel<G, ACC><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
+        LOC_CUDA_TRY(cudaGetLastError());
+        return LOC_OK;
+    }
+};
 
 loc_status launch_march3d(const DevModel &m, const MarchArgs &a, cudaStream_t st)
 {
-    switch (a.per) {
-    case 1: return launch_g<1>(m, a, st);
-    case 2: return launch_g<2>(m, a, st);
-    case 3: return launch_g<3>(m, a, st);
-    case 4: return launch_g<4>(m, a, st);
-    case 5: return launch_g<5>(m, a, st);
-    case 6: return launch_g<6>(m, a, st);
-    case 7: return launch_g<7>(m, a, st);
-    case 8: return launch_g<8>(m, a, st);
-    case 9: return launch_g<9>(m, a, st);
-    case 10: return launch_g<10>(m, a, st);
-    case 11: return launch_g<11>(m, a, st);
-    case 12: return launch_g<12>(m, a, st);
-    case 13: return launch_g<13>(m, a, st);
-    case 14: return launch_g<14>(m, a, st);
-    default: return launch_g<15>(m, a, st);
-    }
+    return march_dispatch(a, Launch3D{m, a, st});
 }
 
 loc_status launch_march(const DevModel &m, const MarchArgs &a, cudaStream_t st)

@@ -33,6 +33,7 @@
 namespace loc {
 
 constexpr int kOctWarpsPerBlock = 4;
+static_assert(kOctWarpsPerBlock <= kWarpsPerBlock, "march_step's per-warp tiles are sized for kWarpsPerBlock warps");
 constexpr int kOctBlocksPerSM = 4;
 constexpr int kOctMaxBlocksPerSM = 8;       // replay: up to 32 warps per SM
 constexpr int kOctMaxDepth = 10;
@@ -322,7 +323,7 @@ struct OctRecVisitor {
 };
 
 // Depth-first traversal of the rays created from root line (i, j).
-template <int G, class V>
+template <int G, int ACC, class V>
 __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo &g, int i, int j,
                              float *I, float *snap, int4 *kids_all, OctFrame *fr, int *path, int lane,
                              V &vis, long long &nw)
@@ -337,6 +338,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
     OctPathCache pc;
     pc.p[0] = pc.p[1] = pc.p[2] = 0;
     pc.L = -1;
+    MarchState pend = march_state();
     if (V::kNeedI) init_ray<G>(m, a, I, lane);
     while (true) {
         bool done_line = cur.z >= g.E;
@@ -411,7 +413,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                 st.s = (float)(int)dz * g.D.unit;       // dz <= one leaf <= 2^24 units
                 st.w = oct_weight(dz, Lc, wscale);
                 load_lines<G>(m, a, st);
-                nw += (long long)march_step<G>(m, a, I, st, lane) * a.n_lines;
+                nw += (long long)march_step<G, ACC>(m, a, I, st, lane, pend) * a.n_lines;
                 __syncwarp();
             } else {
                 vis.step(lane, cur, dz, leaf, Lc);
@@ -422,7 +424,10 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
         }
         // the current line is finished (or paused): start the next new ray of
         // the innermost frame, or resume the line that created them
-        if (depth == 0) break;
+        if (depth == 0) {
+            if (V::kNeedI) march_state_end<ACC>(m, a, pend, lane);
+            break;
+        }
         const int fi = depth - 1;
         OctFrame &f = fr[fi];
         const int nxt = f.next;
@@ -448,7 +453,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
     }
 }
 
-template <int G>
+template <int G, int ACC>
 __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(DevModel m, MarchArgs a0,
                                                                                unsigned *counter)
 {
@@ -481,8 +486,8 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
         g.Lmax = m.Lmax;
         g.E = (long long)m.N << kFixedBits;
         g.o = ((1ll << kFixedBits) >> m.Lmax) / 2;
-        oct_traverse<G>(m, a, g, (int)(r / m.N), (int)(r % m.N), I, snap, kids, frames[wid], paths[wid],
-                        lane, vis, nw);
+        oct_traverse<G, ACC>(m, a, g, (int)(r / m.N), (int)(r % m.N), I, snap, kids, frames[wid], paths[wid],
+                             lane, vis, nw);
     }
     if (a0.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)nw);   // nw counts lines
 }
@@ -538,7 +543,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
         g.D = m.dirs[d];
         vis.local = 0;
         vis.ctrl = 0;
-        oct_traverse<1>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
+        oct_traverse<1, kAccPlain>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
                         paths[wid], lane, vis, nw);
         if (fam_work && lane == 0) fam_work[(long long)d * per_dir + r] = vis.local;
         if (fam_rec && lane == 0) fam_rec[(long long)d * per_dir + r] = vis.local + vis.ctrl;
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) record_octree_kernel(D
         vis.rec = m.oct_rec + r0;
         vis.cap = m.oct_rec_off[it + 1] - r0;
         vis.n = 0;
-        oct_traverse<1>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
+        oct_traverse<1, kAccPlain>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
                         paths[wid], lane, vis, nw);
         if (vis.n != vis.cap && lane == 0) atomicExch(m.oct_err, 4);
     }
@@ -605,7 +610,7 @@ __device__ __forceinline__ void replay_load(const DevModel &m, const MarchArgs &
     load_lines<G>(m, a, st);
 }
 
-template <int G>
+template <int G, int ACC>
 __device__ long long replay_family(const DevModel &m, const MarchArgs &a, const Dir3D &D, long long r0,
                                    long long r1, float *I, float *snap, int lane)
 {
@@ -617,6 +622,7 @@ __device__ long long replay_family(const DevModel &m, const MarchArgs &a, const 
     unsigned long long rb = (b0 + lane < r1) ? rec[b0 + lane] : 0ull;
     unsigned long long rn = (b0 + 32 + lane < r1) ? rec[b0 + 32 + lane] : 0ull;
     Step<G> cur, nxt;
+    MarchState pend = march_state();
     bool pre = false;                                    // cur holds the data of record q
     for (long long q = r0; q < r1; q++) {
         if (q - b0 == 32) {
@@ -634,7 +640,7 @@ __device__ long long replay_family(const DevModel &m, const MarchArgs &a, const 
             if (!pre) replay_load<G>(m, a, D, wscale, x, cur);
             const bool nstep = (q + 1 < r1) && ((unsigned)(y >> 61) == kRecStep);
             if (nstep) replay_load<G>(m, a, D, wscale, y, nxt);
-            nw += (long long)march_step<G>(m, a, I, cur, lane) * a.n_lines;
+            nw += (long long)march_step<G, ACC>(m, a, I, cur, lane, pend) * a.n_lines;
             __syncwarp();
             if (nstep) cur = nxt;
             pre = nstep;
@@ -650,11 +656,14 @@ __device__ long long replay_family(const DevModel &m, const MarchArgs &a, const 
             pre = false;
         }
     }
+    march_state_end<ACC>(m, a, pend, lane);
     return nw;
 }
 
-template <int G>
-__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) replay_octree_kernel(DevModel m, MarchArgs a0,
+// registers capped so that 4 blocks (16 warps) fit per SM, 5 for small line
+// groups
+template <int G, int ACC>
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32, G <= 6 ? 5 : 4) replay_octree_kernel(DevModel m, MarchArgs a0,
                                                                                 unsigned *counter)
 {
     extern __shared__ float smem[];
@@ -676,7 +685,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) replay_octree_kernel(D
         const MarchArgs a = warp_args(m, a0, (int)((long long)it - fam * a0.n_groups));
         const Dir3D D = m.dirs[item / per_dir];
         init_ray<G>(m, a, I, lane);
-        nw += replay_family<G>(m, a, D, m.oct_rec_off[item], m.oct_rec_off[item + 1], I, snap, lane);
+        nw += replay_family<G, ACC>(m, a, D, m.oct_rec_off[item], m.oct_rec_off[item + 1], I, snap, lane);
     }
     if (a0.count && lane == 0) atomicAdd(m.upd_count, (unsigned long long)nw);   // nw counts lines
 }
@@ -802,45 +811,37 @@ static int oct_blocks_per_sm(K kernel, size_t smem)
     return std::max(kOctBlocksPerSM, std::min(nb, kOctMaxBlocksPerSM));
 }
 
-template <int G>
-static loc_status launch_oct_g(const DevModel &m, const MarchArgs &a, unsigned *counter, cudaStream_t st)
-{
-    const size_t smem = (size_t)kOctWarpsPerBlock * a.per * m.n_ch * sizeof(float);
-    if (m.oct_rec) {
-        LOC_CUDA_TRY(cudaFuncSetAttribute(replay_octree_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int blocks = octree_sms() * oct_blocks_per_sm(replay_octree_kernel<G>, smem);
-        replay_octree_kernel<G><<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
-    } else {
-        LOC_CUDA_TRY(cudaFuncSetAttribute(march_octree_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
-        march_octree_kernel<G><<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+struct LaunchOctree {
+    const DevModel &m;
+    const MarchArgs &a;
+    unsigned *counter;
+    cudaStream_t st;
+    template <int G, int ACC>
+    loc_status go() const
+    {
+        const size_t smem = (size_t)kOctWarpsPerBlock * a.per * m.n_ch * sizeof(float);
+        if (m.oct_rec) {
+            auto k = replay_octree_kernel<G, ACC>;
+            LOC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int blocks = octree_sms() * oct_blocks_per_sm(k, smem);
+            k<<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+        } else {
+            auto k = march_octree_kernel<G, ACC>;
+            LOC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
+            k<<<blocks, kOctWarpsPerBlock * 32, smem, st>>>(m, a, counter);
+        }
+        LOC_CUDA_TRY(cudaGetLastError());
+        return LOC_OK;
     }
-    LOC_CUDA_TRY(cudaGetLastError());
-    return LOC_OK;
-}
+};
 
 // counter: one unsigned of device scratch right after the error flag
 loc_status launch_march_octree(const DevModel &m, const MarchArgs &a, cudaStream_t st)
 {
     unsigned *counter = (unsigned *)(m.oct_err + 1);
     LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-    switch (a.per) {
-    case 1: return launch_oct_g<1>(m, a, counter, st);
-    case 2: return launch_oct_g<2>(m, a, counter, st);
-    case 3: return launch_oct_g<3>(m, a, counter, st);
-    case 4: return launch_oct_g<4>(m, a, counter, st);
-    case 5: return launch_oct_g<5>(m, a, counter, st);
-    case 6: return launch_oct_g<6>(m, a, counter, st);
-    case 7: return launch_oct_g<7>(m, a, counter, st);
-    case 8: return launch_oct_g<8>(m, a, counter, st);
-    case 9: return launch_oct_g<9>(m, a, counter, st);
-    case 10: return launch_oct_g<10>(m, a, counter, st);
-    case 11: return launch_oct_g<11>(m, a, counter, st);
-    case 12: return launch_oct_g<12>(m, a, counter, st);
-    case 13: return launch_oct_g<13>(m, a, counter, st);
-    case 14: return launch_oct_g<14>(m, a, counter, st);
-    default: return launch_oct_g<15>(m, a, counter, st);
-    }
+    return march_dispatch(a, LaunchOctree{m, a, counter, st});
 }
 
 loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long long cap,

@@ -76,15 +76,7 @@ __global__ void line_params_kernel(DevModel m, int zero_acc, double cutoff)
     if (idx >= (long long)m.T * m.n_cells) return;
     line_params_one(m, idx, cutoff);
     if (zero_acc) {
-        const bool first = (idx % m.T) == 0;
-        if (zero_acc == 2) {
-            m.acc64[2 * idx] = 0.0;
-            m.acc64[2 * idx + 1] = 0.0;
-            if (first) m.norm64[idx / m.T] = 0.0;
-        } else {
-            m.acc[idx] = make_float2(0.f, 0.f);
-            if (first) m.norm[idx / m.T] = 0.f;
-        }
+        acc_zero(m, idx, idx / m.T, zero_acc == 2, (idx % m.T) == 0);
         if (idx == 0) *m.dtex_bits = 0u;
     }
 }
@@ -111,7 +103,7 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
         double M[LMAX][LMAX + 1];
         for (int i = 0; i < L; i++)
             for (int j = 0; j <= L; j++) M[i][j] = 0.0;
-        const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
+        const double nrm = norm_value(m, c, fp64_acc);
         for (int t = 0; t < m.T; t++) {
             const int u = m.line_u[t], l = m.line_l[t];
             const double A = m.line_A[t];
@@ -122,8 +114,9 @@ __global__ void __launch_bounds__(128) se_thread_kernel(DevModel m, int ali, int
                 beta = 1.0;
             } else if (nrm > 0.0) {
                 double sj, ej;
-                if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
-                else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
+                const double2 a = acc_value(m, o, fp64_acc);
+                sj = a.x;
+                ej = a.y;
                 const double inv_nrm = recip(nrm);
                 J = sj * inv_nrm;
                 beta = ej * inv_nrm;
@@ -301,16 +294,11 @@ __global__ void acc_to_f64_kernel(DevModel m, int fp64_acc, double *sij, double 
         const long long c = idx / m.T;
         const long long t = idx - c * m.T;
         const long long o = t * m.n_cells + c;
-        if (fp64_acc) {
-            if (sij) sij[o] = m.acc64[2 * idx];
-            if (esc) esc[o] = m.acc64[2 * idx + 1];
-        } else {
-            const float2 a = m.acc[idx];
-            if (sij) sij[o] = a.x;
-            if (esc) esc[o] = a.y;
-        }
+        const double2 a = acc_value(m, idx, fp64_acc);
+        if (sij) sij[o] = a.x;
+        if (esc) esc[o] = a.y;
     }
-    if (idx < m.n_cells && norm) norm[idx] = fp64_acc ? m.norm64[idx] : (double)m.norm[idx];
+    if (idx < m.n_cells && norm) norm[idx] = norm_value(m, idx, fp64_acc);
 }
 
 loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,

@@ -85,15 +85,7 @@ __device__ __forceinline__ void next_line_params(const DevModel &m, long long c,
                                                  int fp64_acc, double cutoff, bool first)
 {
     line_params_at(m, c, t, xn[m.line_l[t]], xn[m.line_u[t]], cutoff);
-    const long long o = c * m.T + t;
-    if (fp64_acc) {
-        m.acc64[2 * o] = 0.0;
-        m.acc64[2 * o + 1] = 0.0;
-        if (first) m.norm64[c] = 0.0;
-    } else {
-        m.acc[o] = make_float2(0.f, 0.f);
-        if (first) m.norm[c] = 0.f;
-    }
+    acc_zero(m, c * m.T + t, c, fp64_acc, first);
 }
 
 __device__ __forceinline__ double tex_of(const DevModel &m, int t, const double *x)
@@ -148,7 +140,7 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
     const int L = m.L;
     for (int i = sl; i < L * W; i += LW) M[i] = 0.0;
     __syncwarp();
-    const double nrm = fp64_acc ? m.norm64[c] : (double)m.norm[c];
+    const double nrm = norm_value(m, c, fp64_acc);
     const double inv_nrm = (nrm > 0.0) ? recip(nrm) : 0.0;
     for (int b = 0; b < m.T; b += LW) {
         const int t = b + sl;
@@ -162,8 +154,9 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
                 beta = 1.0;
             } else if (nrm > 0.0) {
                 double sj, ej;
-                if (fp64_acc) { sj = m.acc64[2 * o]; ej = m.acc64[2 * o + 1]; }
-                else { const float2 a = m.acc[o]; sj = a.x; ej = a.y; }
+                const double2 a = acc_value(m, o, fp64_acc);
+                sj = a.x;
+                ej = a.y;
                 J = sj * inv_nrm;
                 beta = ej * inv_nrm;
                 if (!ali) { J = J + (double)m.ks[o].y * (1.0 - beta); beta = 1.0; }

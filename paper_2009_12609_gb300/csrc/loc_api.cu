@@ -452,11 +452,16 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
     TRY(upload<float2>(m, &D.ks, nullptr, nc * D.T, m->mol_mem, "line parameters"));
     TRY(upload<float2>(m, &D.acc, nullptr, nc * D.T, m->mol_mem, "accumulators"));
     TRY(upload<float>(m, &D.norm, nullptr, nc, m->mol_mem, "norm"));
+    TRY(upload<float2>(m, &D.acc_c, nullptr, nc * D.T, m->mol_mem, "accumulator compensation"));
+    TRY(upload<float>(m, &D.norm_c, nullptr, nc, m->mol_mem, "norm compensation"));
+    LOC_CUDA_TRY(cudaMemsetAsync(D.acc_c, 0, sizeof(float2) * nc * D.T, m->st));
+    LOC_CUDA_TRY(cudaMemsetAsync(D.norm_c, 0, sizeof(float) * nc, m->st));
     TRY(upload<double>(m, &D.acc64, nullptr, 2 * nc * D.T, m->mol_mem, "accumulators64"));
     TRY(upload<double>(m, &D.norm64, nullptr, nc, m->mol_mem, "norm64"));
     TRY(upload<unsigned int>(m, &D.dtex_bits, nullptr, 1, m->mol_mem, "dtex"));
     TRY(upload<unsigned long long>(m, &D.maser_count, nullptr, 1, m->mol_mem, "maser count"));
     TRY(upload<unsigned long long>(m, &D.upd_count, nullptr, 1, m->mol_mem, "update count"));
+    TRY(upload<unsigned long long>(m, &D.nom_count, nullptr, 1, m->mol_mem, "nominal update count"));
     // collision rates depend only on n_H2 and T_kin: tabulated once when the
     // table (16 B per cell and pair) takes at most a quarter of the free
     // device memory and 16 GiB, else computed inside every solve (an FP64
@@ -522,7 +527,8 @@ static loc_status check_opts(const loc_iter_opts *o)
     CHECK(o, "NULL options");
     CHECK(o->max_iter >= 1, "max_iter must be >= 1");
     CHECK(o->tol_tex >= 0.0 && std::isfinite(o->tol_tex), "tol_tex must be >= 0");
-    CHECK(o->precision == LOC_FP32_MARCH || o->precision == LOC_FP64_ACC, "unknown precision");
+    CHECK(o->precision == LOC_FP32_MARCH || o->precision == LOC_FP64_ACC || o->precision == LOC_FP32_PLAIN,
+          "unknown precision");
     CHECK(o->lines_per_pass >= 0, "lines_per_pass must be >= 0");
     CHECK(o->window_sigmas >= 0.0 && std::isfinite(o->window_sigmas), "window_sigmas must be >= 0");
     CHECK(o->profile == 0 || o->profile == 1, "profile must be 0 or 1");
@@ -633,6 +639,8 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
     } else {
         LOC_CUDA_TRY(cudaMemsetAsync(D.acc, 0, sizeof(float2) * D.T * D.n_cells, m->st));
         LOC_CUDA_TRY(cudaMemsetAsync(D.norm, 0, sizeof(float) * D.n_cells, m->st));
+        LOC_CUDA_TRY(cudaMemsetAsync(D.acc_c, 0, sizeof(float2) * D.T * D.n_cells, m->st));
+        LOC_CUDA_TRY(cudaMemsetAsync(D.norm_c, 0, sizeof(float) * D.n_cells, m->st));
     }
     MarchArgs a;
     memset(&a, 0, sizeof(a));
@@ -678,6 +686,7 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
     }
     a.n_groups = (D.T + a.per - 1) / a.per;
     a.fp64_acc = fp64;
+    a.comp = o->precision == LOC_FP32_MARCH;
     a.count = o->profile;
     if (run > 0) {
         if (a.n_chunks > 0) TRY(launch_march1d_chunked(D, a, m->st));
@@ -794,6 +803,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     LOC_CUDA_TRY(cudaEventCreate(&e1));
     LOC_CUDA_TRY(cudaMemsetAsync(D.maser_count, 0, sizeof(unsigned long long), m->st));
     LOC_CUDA_TRY(cudaMemsetAsync(D.upd_count, 0, sizeof(unsigned long long), m->st));
+    LOC_CUDA_TRY(cudaMemsetAsync(D.nom_count, 0, sizeof(unsigned long long), m->st));
     LOC_CUDA_TRY(cudaEventRecord(e0, m->st));
     int it = 0;
     float dtex = 0.f;
@@ -878,9 +888,10 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         r->segments = m->segs_per_sim;
         r->updates = (double)m->segs_per_sim * D.n_ch * D.T * it;
         r->kernel_ms = ms;
-        unsigned long long mc = 0, uc = 0;
+        unsigned long long mc = 0, uc = 0, nc = 0;
         cudaMemcpy(&mc, D.maser_count, sizeof(mc), cudaMemcpyDeviceToHost);
         cudaMemcpy(&uc, D.upd_count, sizeof(uc), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&nc, D.nom_count, sizeof(nc), cudaMemcpyDeviceToHost);
         r->n_maser_cells = (int64_t)mc;
         r->path_records = m->path_records;
         r->coll_table = D.coll_rates ? 1 : 0;
@@ -890,6 +901,7 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
             r->params_ms = t_par;
             r->march_launches = (int64_t)it;
             r->computed_updates = (double)uc;
+            r->nominal_updates = (double)nc;
         }
     }
     if (o->tol_tex > 0.0 && !converged) {

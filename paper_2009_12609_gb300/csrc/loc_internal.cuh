@@ -105,11 +105,14 @@ struct DevModel {
     float2 *ks;                         // [n_cells][T] {K (per unit phi and length), S}
     float2 *acc;                        // [n_cells][T] {SIJ, ESC}
     float *norm;                        // [n_cells]
+    float2 *acc_c;                      // [n_cells][T] rounding errors of acc's additions (or null)
+    float *norm_c;                      // [n_cells] rounding errors of norm's additions (or null)
     double *acc64;                      // [n_cells][T][2] (FP64 accumulation)
     double *norm64;                     // [n_cells]
     unsigned int *dtex_bits;            // device scalar: max rel dTex (float bits)
     unsigned long long *maser_count;    // device scalar
     unsigned long long *upd_count;      // device scalar: computed updates (profiling)
+    unsigned long long *nom_count;      // device scalar: nominal updates (profiling)
 };
 
 // Parameters of one march launch.
@@ -121,6 +124,7 @@ struct MarchArgs {
     float window;       // window half-width in sigma (0 = all channels)
     float inv_dv;       // 1 / channel width (s/cm)
     int fp64_acc;       // accumulate in FP64
+    int comp;           // FP32 accumulation compensated (acc_c, norm_c collect the rounding errors)
     int do_norm;        // the warp also accumulates NORM (group 0)
     int count;          // count computed channel updates into upd_count
     // 1D rays cut into runs of `chunk` consecutive steps (0: whole rays);
@@ -133,6 +137,44 @@ struct MarchArgs {
     int2 *run_rng;          // [n_chunks] channels [lo, hi) the run's step windows touch
     int tile;               // channels per shared-memory tile of the run maps (>= every run's union)
 };
+
+// ----------------------------------------------------------------------------
+// Per-cell accumulators as the solve reads them: the FP32 sums plus the
+// rounding errors of their additions (compensated accumulation), or the FP64
+// sums of the FP64-accumulation mode.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double2 acc_value(const DevModel &m, long long o, int fp64_acc)
+{
+    if (fp64_acc) return make_double2(m.acc64[2 * o], m.acc64[2 * o + 1]);
+    const float2 a = m.acc[o];
+    if (!m.acc_c) return make_double2(a.x, a.y);
+    const float2 e = m.acc_c[o];
+    return make_double2((double)a.x + (double)e.x, (double)a.y + (double)e.y);
+}
+
+__device__ __forceinline__ double norm_value(const DevModel &m, long long c, int fp64_acc)
+{
+    if (fp64_acc) return m.norm64[c];
+    const double n = m.norm[c];
+    return m.norm_c ? n + (double)m.norm_c[c] : n;
+}
+
+// clears the accumulators of entry o = c T + t (and NORM of cell c if first)
+__device__ __forceinline__ void acc_zero(const DevModel &m, long long o, long long c, int fp64_acc, bool first)
+{
+    if (fp64_acc) {
+        m.acc64[2 * o] = 0.0;
+        m.acc64[2 * o + 1] = 0.0;
+        if (first) m.norm64[c] = 0.0;
+    } else {
+        m.acc[o] = make_float2(0.f, 0.f);
+        if (m.acc_c) m.acc_c[o] = make_float2(0.f, 0.f);
+        if (first) {
+            m.norm[c] = 0.f;
+            if (m.norm_c) m.norm_c[c] = 0.f;
+        }
+    }
+}
 
 // ----------------------------------------------------------------------------
 // host-side helpers (implemented in loc_api.cu)

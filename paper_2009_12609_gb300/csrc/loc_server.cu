@@ -44,7 +44,7 @@ struct ArenaLayout {
     size_t n_h2, t_kin, abundance, sigma, radius, v1d, energy, g, line_u, line_l, line_A, line_nu,
         coll_u, coll_l, coll_k;       // uploaded inputs (contiguous prefix)
     size_t inputs_end;
-    size_t inv, ray_off, segs, tan, W, nbg, nbg64, x, x_new, ks, acc, norm, dtex, maser, upd, coll;
+    size_t inv, ray_off, segs, tan, W, nbg, nbg64, x, x_new, ks, acc, norm, acc_c, norm_c, dtex, maser, upd, coll;
     size_t total;
 };
 
@@ -93,7 +93,8 @@ static ArenaLayout layout_for(const Request &q)
     a.inv = put(4 * K); a.ray_off = put(4 * (R + 1)); a.segs = put(sizeof(Seg1D) * 2 * R * (K + 1));
     a.tan = put(4 * R); a.W = put(8 * K); a.nbg = put(4 * T); a.nbg64 = put(8 * T);
     a.x = put(8 * K * L); a.x_new = put(8 * K * L); a.ks = put(8 * K * T); a.acc = put(8 * K * T);
-    a.norm = put(4 * K); a.dtex = put(4); a.maser = put(8); a.upd = put(8);
+    a.norm = put(4 * K); a.acc_c = put(8 * K * T); a.norm_c = put(4 * K);
+    a.dtex = put(4); a.maser = put(8); a.upd = put(8);
     a.coll = put(16 * K * (P ? P : 1));   // collision rates per cell and pair, tabulated once
     a.total = o;
     return a;
@@ -298,6 +299,8 @@ static bool admit(loc_server *s, int si, Request *q)
     m.ks = (float2 *)(b + a.ks);
     m.acc = (float2 *)(b + a.acc);
     m.norm = (float *)(b + a.norm);
+    m.acc_c = (float2 *)(b + a.acc_c);
+    m.norm_c = (float *)(b + a.norm_c);
     m.dtex_bits = (unsigned *)(b + a.dtex);
     m.maser_count = (unsigned long long *)(b + a.maser);
     m.upd_count = (unsigned long long *)(b + a.upd);

@@ -32,6 +32,7 @@ LOC_OCTREE_3D = 3
 
 LOC_FP32_MARCH = 0
 LOC_FP64_ACC = 1
+LOC_FP32_PLAIN = 2
 
 _d = ctypes.POINTER(ctypes.c_double)
 _i32 = ctypes.POINTER(ctypes.c_int32)
@@ -81,7 +82,8 @@ class loc_iter_report(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("n_maser_cells", ctypes.c_int64),
                 ("march_ms", ctypes.c_double), ("se_ms", ctypes.c_double),
                 ("params_ms", ctypes.c_double), ("march_launches", ctypes.c_int64),
-                ("computed_updates", ctypes.c_double), ("path_records", ctypes.c_int64),
+                ("computed_updates", ctypes.c_double), ("nominal_updates", ctypes.c_double),
+                ("path_records", ctypes.c_int64),
                 ("coll_table", ctypes.c_int)]
 
 
@@ -294,7 +296,7 @@ def molecule_desc(mol, keep, n_levels=None):
 
 def iter_opts(max_iter=1, tol_tex=0.0, ali=True, precision="fp32", lines_per_pass=0,
               window_sigmas=0.0, profile=False, steps_per_chunk=0, level_cutoff=0.0):
-    prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC}[precision]
+    prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC, "fp32plain": LOC_FP32_PLAIN}[precision]
     return loc_iter_opts(int(max_iter), float(tol_tex), int(bool(ali)), prec,
                          int(lines_per_pass), float(window_sigmas), int(bool(profile)),
                          int(steps_per_chunk), float(level_cutoff))
@@ -346,7 +348,8 @@ def loc_iterate(h, **opts):
                 segments=r.segments, updates=r.updates, kernel_ms=r.kernel_ms,
                 n_maser_cells=r.n_maser_cells, march_ms=r.march_ms, se_ms=r.se_ms,
                 params_ms=r.params_ms, march_launches=r.march_launches,
-                computed_updates=r.computed_updates, path_records=r.path_records,
+                computed_updates=r.computed_updates, nominal_updates=r.nominal_updates,
+                path_records=r.path_records,
                 coll_table=r.coll_table)
 
 
