@@ -195,6 +195,13 @@ typedef struct loc_molecule_desc {
  *                 saving grows as lines_per_pass shrinks.  At most 1e-6
  *                 (below the convergence metric's 1e-6 population floor).
  *                 Emergent spectra and maps never truncate.
+ *  dir_begin, dir_end  3D models: the ray simulation covers directions
+ *                 [dir_begin, dir_end) of the model's table only (both 0:
+ *                 all).  The directions of one simulation are independent
+ *                 (Sect. 2.2), so N devices can each march a share and sum
+ *                 their accumulators (loc_radiation_buffers) before
+ *                 loc_solve; loc_iterate with a range solves from that
+ *                 share alone.  Ignored for 1D models.
  */
 typedef struct loc_iter_opts {
     int max_iter;
@@ -206,6 +213,7 @@ typedef struct loc_iter_opts {
     int profile;
     int steps_per_chunk;
     double level_cutoff;
+    int dir_begin, dir_end;
 } loc_iter_opts;
 
 /* Iteration report. */
@@ -282,6 +290,38 @@ loc_status loc_autotune(loc_model *m, const loc_iter_opts *o, int *best_per, int
 loc_status loc_get_radiation(const loc_model *m, double *sij, double *esc,
                              double *norm, size_t n_out_lines_cells,
                              size_t n_out_cells);
+
+/* Device addresses of a model's per-cell accumulators, valid until the
+ * model is destroyed (loc_set_molecule reallocates them).  All are DEVICE
+ * pointers owned by the library:
+ *  acc, acc_c     [n_cells][n_lines][2] FP32 {SIJ, ESC} and the
+ *                 compensation words of their additions (zero unless the
+ *                 precision is LOC_FP32_MARCH);
+ *  norm, norm_c   [n_cells] FP32 NORM and its compensation word;
+ *  acc64, norm64  the FP64 accumulators of LOC_FP64_ACC, same layout.
+ * Every array is a plain sum over ray steps, so the accumulators of several
+ * devices that marched disjoint direction ranges of the same model combine
+ * by element-wise addition of each array (an all-reduce with sum), after
+ * which loc_solve gives every device the populations of the whole ray
+ * simulation.  Reading or writing them while the model's stream has work
+ * queued races with that work. */
+typedef struct loc_radiation_buffers_t {
+    int64_t n_cells;
+    int n_lines;
+    float *acc, *acc_c, *norm, *norm_c;
+    double *acc64, *norm64;
+} loc_radiation_buffers_t;
+
+loc_status loc_radiation_buffers(loc_model *m, loc_radiation_buffers_t *out);
+
+/* The statistical-equilibrium half of one ALI iteration (Sect. 2): every
+ * cell's rate equations from the accumulators as they are now (after
+ * loc_march, and after any summation of several devices' accumulators),
+ * the new populations in place of the old, and the convergence metric
+ * between them in r->max_rel_dtex (r may be NULL).  o->ali, o->precision
+ * (which must be the last march's) and o->level_cutoff apply.  LOC_ESTATE
+ * if no ray simulation has run. */
+loc_status loc_solve(loc_model *m, const loc_iter_opts *o, loc_iter_report *r);
 
 /* Level populations x[cell][level] (fractions summing to 1 per cell). */
 loc_status loc_get_populations(const loc_model *m, double *out, size_t n_out);

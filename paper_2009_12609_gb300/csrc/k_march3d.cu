@@ -13,11 +13,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m
     const int wid = threadIdx.x >> 5;
     const long long item0 = (long long)blockIdx.x * kWarpsPerBlock + wid;
     const long long per_dir = (long long)m.N * m.N;
-    if (item0 >= per_dir * m.n_dir * a0.n_groups) return;
+    if (item0 >= per_dir * (a0.dir1 - a0.dir0) * a0.n_groups) return;
     const long long item = item0 / a0.n_groups;
     const MarchArgs a = warp_args(m, a0, (int)(item0 - item * a0.n_groups));
-    const int dir = (int)(item / per_dir);
-    const long long r = item - (long long)dir * per_dir;
+    const int dir = a0.dir0 + (int)(item / per_dir);
+    const long long r = item - (long long)(dir - a0.dir0) * per_dir;
     const long long i = r / m.N, j = r - (r / m.N) * m.N;
     float *I = smem + (size_t)wid * a.per * m.n_ch;
     init_ray<G>(m, a, I, lane);
@@ -60,7 +60,7 @@ struct Launch3D {
     loc_status go() const
     {
         const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
-        const long long items = (long long)m.N * m.N * m.n_dir * a.n_groups;
+        const long long items = (long long)m.N * m.N * (a.dir1 - a.dir0) * a.n_groups;
         const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
         LOC_CUDA_TRY(cudaFuncSetAttribute(march3d_kernel<G, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         march3d_kernel<G, ACC><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);

@@ -477,8 +477,9 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) march_octree_kernel(De
         if ((long long)it >= total) break;
         const long long fam = (long long)it / a0.n_groups;     // most work first
         const long long item = m.oct_order ? (long long)m.oct_order[fam] : fam;
-        const MarchArgs a = warp_args(m, a0, (int)((long long)it - fam * a0.n_groups));
         const int dir = (int)(item / per_dir);
+        if (dir < a0.dir0 || dir >= a0.dir1) continue;          // another rank's direction
+        const MarchArgs a = warp_args(m, a0, (int)((long long)it - fam * a0.n_groups));
         const long long r = item - (long long)dir * per_dir;
         OctGeo g;
         g.D = m.dirs[dir];
@@ -682,8 +683,10 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32, G <= 6 ? 5 : 4) replay
         if ((long long)it >= total) break;
         const long long fam = (long long)it / a0.n_groups;     // most work first
         const long long item = m.oct_order ? (long long)m.oct_order[fam] : fam;
+        const int dir = (int)(item / per_dir);
+        if (dir < a0.dir0 || dir >= a0.dir1) continue;          // another rank's direction
         const MarchArgs a = warp_args(m, a0, (int)((long long)it - fam * a0.n_groups));
-        const Dir3D D = m.dirs[item / per_dir];
+        const Dir3D D = m.dirs[dir];
         init_ray<G>(m, a, I, lane);
         nw += replay_family<G, ACC>(m, a, D, m.oct_rec_off[item], m.oct_rec_off[item + 1], I, snap, lane);
     }

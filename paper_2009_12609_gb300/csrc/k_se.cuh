@@ -169,13 +169,27 @@ __device__ __forceinline__ float se_seg_cell(const DevModel &m, long long c, boo
         }
     }
     __syncwarp();
-    for (int b = 0; b < m.P; b += LW) {
-        const int p = b + sl;
-        if (p < m.P) {
-            const int u = m.coll_u[p], l = m.coll_l[p];
-            const double2 cr = coll_rate(m, c, p);
-            M[l * W + u] += cr.x;
-            M[u * W + l] += cr.y;
+    // collision rates: the pairs of four rounds are fetched before any is
+    // added (independent loads in flight instead of one load per round trip)
+    for (int b = 0; b < m.P; b += 4 * LW) {
+        double2 cr[4];
+        int pu[4], pl[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int p = b + q * LW + sl;
+            pu[q] = -1;
+            if (p < m.P) {
+                pu[q] = m.coll_u[p];
+                pl[q] = m.coll_l[p];
+                cr[q] = coll_rate(m, c, p);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (pu[q] >= 0) {
+                M[pl[q] * W + pu[q]] += cr[q].x;
+                M[pu[q] * W + pl[q]] += cr[q].y;
+            }
         }
     }
     __syncwarp();

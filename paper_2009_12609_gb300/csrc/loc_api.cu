@@ -533,6 +533,7 @@ static loc_status check_opts(const loc_iter_opts *o)
     CHECK(o->window_sigmas >= 0.0 && std::isfinite(o->window_sigmas), "window_sigmas must be >= 0");
     CHECK(o->profile == 0 || o->profile == 1, "profile must be 0 or 1");
     CHECK(o->level_cutoff >= 0.0 && o->level_cutoff <= 1e-6, "level_cutoff must be in [0, 1e-6]");
+    CHECK(o->dir_begin >= 0 && o->dir_end >= 0, "direction range must be >= 0");
     return LOC_OK;
 }
 
@@ -648,6 +649,14 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
     const int run = steps_per_run(m, o, a.per);
     a.window = (float)o->window_sigmas;
     a.inv_dv = (float)(1.0 / D.dv);
+    a.dir0 = 0;
+    a.dir1 = D.n_dir;
+    if (D.geometry != LOC_SHELLS_1D && (o->dir_begin != 0 || o->dir_end != 0)) {
+        CHECK(o->dir_begin >= 0 && o->dir_begin < o->dir_end && o->dir_end <= D.n_dir,
+              "direction range [%d, %d) outside [0, %d) or empty", o->dir_begin, o->dir_end, D.n_dir);
+        a.dir0 = o->dir_begin;
+        a.dir1 = o->dir_end;
+    }
     if (run > 0) {
         TRY(ensure_runs(m, run));
         a.chunk = run;
@@ -933,6 +942,61 @@ loc_status loc_get_radiation(const loc_model *m, double *sij, double *esc, doubl
     }
     cudaFree(buf);
     return s;
+}
+
+loc_status loc_radiation_buffers(loc_model *m, loc_radiation_buffers_t *out)
+{
+    if (!m || !out) { set_error("NULL argument"); return LOC_EINVAL; }
+    if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
+    const DevModel &D = m->d;
+    memset(out, 0, sizeof(*out));
+    out->n_cells = D.n_cells;
+    out->n_lines = D.T;
+    out->acc = (float *)D.acc;
+    out->acc_c = (float *)D.acc_c;
+    out->norm = D.norm;
+    out->norm_c = D.norm_c;
+    out->acc64 = D.acc64;
+    out->norm64 = D.norm64;
+    return LOC_OK;
+}
+
+// The statistical-equilibrium half of an ALI iteration: the solve of every
+// cell from the accumulators as they are now (after loc_march, and after
+// the caller summed the accumulators of several devices' marches), the
+// convergence metric against the populations before, and the new
+// populations in place.
+loc_status loc_solve(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
+{
+    if (!m) { set_error("NULL model"); return LOC_EINVAL; }
+    TRY(check_opts(o));
+    if (!m->has_mol) { set_error("loc_set_molecule has not been called"); return LOC_ESTATE; }
+    if (!m->has_rad) { set_error("no ray simulation has run"); return LOC_ESTATE; }
+    DevModel &D = m->d;
+    if ((o->precision == LOC_FP64_ACC) != (m->last_fp64 != 0)) {
+        set_error("precision differs from the last ray simulation's");
+        return LOC_EINVAL;
+    }
+    D.trunc = o->level_cutoff > 0.0 ? 1 : 0;
+    LOC_CUDA_TRY(cudaMemsetAsync(D.dtex_bits, 0, sizeof(unsigned), m->st));
+    loc_status st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st, 1, 0, o->level_cutoff);
+    D.trunc = 0;
+    TRY(st);
+    std::swap(D.x, D.x_new);
+    unsigned bits = 0;
+    LOC_CUDA_TRY(cudaMemcpyAsync(&bits, D.dtex_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    float dtex = 0.f;
+    memcpy(&dtex, &bits, sizeof(float));
+    if (r) {
+        memset(r, 0, sizeof(*r));
+        r->iterations = 1;
+        r->max_rel_dtex = dtex;
+        r->segments = m->segs_per_sim;
+        r->path_records = m->path_records;
+        r->coll_table = D.coll_rates ? 1 : 0;
+    }
+    return LOC_OK;
 }
 
 loc_status loc_get_populations(const loc_model *m, double *out, size_t n_out)

@@ -136,6 +136,7 @@ struct MarchArgs {
     float2 *ab;             // [n_chunks][T][n_ch] run maps {alpha, beta}, then {I_in, -}
     int2 *run_rng;          // [n_chunks] channels [lo, hi) the run's step windows touch
     int tile;               // channels per shared-memory tile of the run maps (>= every run's union)
+    int dir0, dir1;         // 3D: the march covers directions [dir0, dir1) of the model's table
 };
 
 // ----------------------------------------------------------------------------

@@ -73,7 +73,8 @@ class loc_iter_opts(ctypes.Structure):
                 ("ali", ctypes.c_int), ("precision", ctypes.c_int),
                 ("lines_per_pass", ctypes.c_int), ("window_sigmas", ctypes.c_double),
                 ("profile", ctypes.c_int), ("steps_per_chunk", ctypes.c_int),
-                ("level_cutoff", ctypes.c_double)]
+                ("level_cutoff", ctypes.c_double), ("dir_begin", ctypes.c_int),
+                ("dir_end", ctypes.c_int)]
 
 
 class loc_iter_report(ctypes.Structure):
@@ -85,6 +86,12 @@ class loc_iter_report(ctypes.Structure):
                 ("computed_updates", ctypes.c_double), ("nominal_updates", ctypes.c_double),
                 ("path_records", ctypes.c_int64),
                 ("coll_table", ctypes.c_int)]
+
+
+class loc_radiation_buffers_t(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_lines", ctypes.c_int),
+                ("acc", _vp), ("acc_c", _vp), ("norm", _vp), ("norm_c", _vp),
+                ("acc64", _vp), ("norm64", _vp)]
 
 
 class loc_server_opts(ctypes.Structure):
@@ -123,7 +130,8 @@ EXPORTS = ["loc_last_error", "loc_version", "loc_create_model", "loc_set_molecul
            "loc_trace_ray", "loc_sync", "loc_destroy", "loc_reset_populations",
            "loc_radiation1d_noalloc", "loc_autotune", "loc_server_create",
            "loc_server_submit", "loc_server_poll", "loc_server_stats", "loc_server_destroy",
-           "loc_trace_octree", "loc_octree_path_sums", "loc_map3d", "loc_check_recip"]
+           "loc_trace_octree", "loc_octree_path_sums", "loc_map3d", "loc_check_recip",
+           "loc_radiation_buffers", "loc_solve"]
 
 
 def library_path():
@@ -295,11 +303,13 @@ def molecule_desc(mol, keep, n_levels=None):
 
 
 def iter_opts(max_iter=1, tol_tex=0.0, ali=True, precision="fp32", lines_per_pass=0,
-              window_sigmas=0.0, profile=False, steps_per_chunk=0, level_cutoff=0.0):
+              window_sigmas=0.0, profile=False, steps_per_chunk=0, level_cutoff=0.0,
+              dir_range=(0, 0)):
     prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC, "fp32plain": LOC_FP32_PLAIN}[precision]
     return loc_iter_opts(int(max_iter), float(tol_tex), int(bool(ali)), prec,
                          int(lines_per_pass), float(window_sigmas), int(bool(profile)),
-                         int(steps_per_chunk), float(level_cutoff))
+                         int(steps_per_chunk), float(level_cutoff), int(dir_range[0]),
+                         int(dir_range[1]))
 
 
 # --------------------------------------------------------------------------
@@ -351,6 +361,24 @@ def loc_iterate(h, **opts):
                 computed_updates=r.computed_updates, nominal_updates=r.nominal_updates,
                 path_records=r.path_records,
                 coll_table=r.coll_table)
+
+
+def loc_solve(h, **opts):
+    o = iter_opts(**opts)
+    r = loc_iter_report()
+    _check(load().loc_solve(h, ctypes.byref(o), ctypes.byref(r)))
+    return dict(iterations=r.iterations, max_rel_dtex=r.max_rel_dtex)
+
+
+def loc_radiation_buffers(h):
+    """Device addresses and element counts of the accumulators:
+    {name: (address, n_elements, numpy dtype)}."""
+    b = loc_radiation_buffers_t()
+    _check(load().loc_radiation_buffers(h, ctypes.byref(b)))
+    nlc, nc = 2 * b.n_cells * b.n_lines, b.n_cells
+    return {"acc": (b.acc, nlc, np.float32), "acc_c": (b.acc_c, nlc, np.float32),
+            "norm": (b.norm, nc, np.float32), "norm_c": (b.norm_c, nc, np.float32),
+            "acc64": (b.acc64, nlc, np.float64), "norm64": (b.norm64, nc, np.float64)}
 
 
 def loc_autotune(h, **opts):
@@ -497,6 +525,16 @@ class Model:
 
     def march(self, **opts):
         loc_march(self.h, **opts)
+
+    def solve(self, **opts):
+        return loc_solve(self.h, **opts)
+
+    def n_dir(self):
+        """Directions of the model's table (1 for 1D models)."""
+        return len(self.model["dirs"]) if "dirs" in self.model else 1
+
+    def radiation_buffers(self):
+        return loc_radiation_buffers(self.h)
 
     def radiation(self):
         return loc_get_radiation(self.h)

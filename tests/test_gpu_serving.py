@@ -158,3 +158,26 @@ def test_server_errors(loc):
         assert e.value.status == loc.LOC_EINVAL
     with pytest.raises(loc.LocError):
         loc.Server(max_slots=0)
+
+
+def test_largest_request_shape_in_a_batch(loc, oracle):
+    """The serving stream's largest request shape (1024 shells, 512 channels,
+    20 levels / 19 lines) batched with three smaller requests: its
+    populations equal the single-model path (2e-5) and its T_ex the FP64
+    oracle (1e-4) after 3 iterations."""
+    big = dict(model=LI.cloud1d_rotor(K=1024, n_ch=512, seed=77, r_clamp_frac=0.05), n_levels=20)
+    reqs = [big] + _requests(3, seed=707)
+    n_iter, window = 3, 8.0
+    with loc.Server(max_slots=8, iters_per_launch=3, window_sigmas=window) as srv:
+        tickets = [srv.submit(r["model"], LI.rotor_molecule(n_levels=r["n_levels"]), max_iter=n_iter)
+                   for r in reqs]
+        results = [srv.poll(t, timeout_ms=300000) for t in tickets]
+    for r, (res, x) in zip(reqs, results):
+        assert res["status"] == 0 and res["iterations"] == n_iter
+        np.testing.assert_allclose(x, _single(loc, r, n_iter, window), rtol=2e-5, atol=1e-14)
+    mol = LI.rotor_molecule(n_levels=20)
+    xr, _ = oracle.iterate_1d(mol, big["model"], n_iter)
+    x = results[0][1]
+    tg, tr = oracle.tex(mol, x), oracle.tex(mol, xr)
+    sel = xr[:, mol["line_u"]].T >= 1e-6
+    assert np.max(np.abs(tg[sel] / tr[sel] - 1.0)) < 1e-4
