@@ -185,6 +185,50 @@ def march_1d(mol, model, Kp, S, n_levels=None):
     return SIJ, ESC, NORM
 
 
+def march_1d_rays(mol, model, Kp, S, j_end, n_levels=None):
+    """The ray simulation of rays j < j_end only (weights from all rays)."""
+    lib = _load()
+    M = _Mol(mol, n_levels)
+    K = len(model["radius"])
+    SIJ = np.zeros((M.T, K))
+    ESC = np.zeros((M.T, K))
+    NORM = np.zeros(K)
+    lib.lo_march_1d_rays(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["t_kin"])),
+                         _p(_f64(model["sigma_turb"])), _p(_f64(model["v"])),
+                         int(model["n_ch"]), ctypes.c_double(model["v_min"]),
+                         ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
+                         ctypes.c_double(model["t_bg"]), _p(_f64(Kp)), _p(_f64(S)), int(j_end),
+                         _p(SIJ), _p(ESC), _p(NORM))
+    return SIJ, ESC, NORM
+
+
+def sub_rays_1d(model, k_sub):
+    """Number of rays (j < j_end) that cross the k_sub innermost shells."""
+    lib = _load()
+    R = _f64(model["radius"])
+    return lib.lo_sub_rays_1d(len(R), _p(R), int(model["n_rays"]), _ray_power(model), int(k_sub))
+
+
+def iterate_1d_sub(mol, model, n_iter, n_sub, k_sub, ali=True, x0=None, n_levels=None):
+    """n_iter ALI iterations, each followed by n_sub sub-iterations of the
+    k_sub innermost shells.  Returns (x, dtex[n_iter])."""
+    lib = _load()
+    M = _Mol(mol, n_levels)
+    K = len(model["radius"])
+    x = lte_populations(mol, model["t_kin"], n_levels) if x0 is None else _f64(x0).copy()
+    dt = np.zeros(max(1, n_iter))
+    bad = lib.lo_iterate_1d_sub(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["n_h2"])),
+                                _p(_f64(model["t_kin"])), _p(_f64(model["sigma_turb"])),
+                                _p(_f64(model["abundance"])), _p(_f64(model["v"])),
+                                int(model["n_ch"]), ctypes.c_double(model["v_min"]),
+                                ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
+                                ctypes.c_double(model["t_bg"]), int(bool(ali)), int(n_iter),
+                                int(n_sub), int(k_sub), _p(x), _p(dt))
+    if bad:
+        raise ArithmeticError(f"{bad} singular rate matrices")
+    return x, dt[:n_iter]
+
+
 def line_off(mol, x, cutoff, n_levels=None):
     """Per-cell line truncation mask [line][cell] (uint8) for populations x."""
     lib = _load()

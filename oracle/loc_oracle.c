@@ -281,11 +281,29 @@ void lo_weights_1d(int K, const double *R, int n_rays, double ray_power, double 
  * lo_step, and each step's contribution carries the weight
  * w = A_j s / W_c (so that sum(w) = 1 per cell).  Outputs SIJ, ESC
  * [line][cell] and NORM [cell], zeroed here. */
+/* The same ray simulation restricted to rays j < j_end (the weights W_c
+ * still come from all n_rays rays). */
+void lo_march_1d_rays(const lo_molecule *m, int K, const double *R,
+                      const double *t_kin, const double *sigma_turb,
+                      const double *v, int n_ch, double v_min, double dv,
+                      int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
+                      int j_end, double *SIJ, double *ESC, double *NORM);
+
 void lo_march_1d(const lo_molecule *m, int K, const double *R,
                  const double *t_kin, const double *sigma_turb,
                  const double *v, int n_ch, double v_min, double dv,
                  int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
                  double *SIJ, double *ESC, double *NORM)
+{
+    lo_march_1d_rays(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S,
+                     n_rays, SIJ, ESC, NORM);
+}
+
+void lo_march_1d_rays(const lo_molecule *m, int K, const double *R,
+                      const double *t_kin, const double *sigma_turb,
+                      const double *v, int n_ch, double v_min, double dv,
+                      int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
+                      int j_end, double *SIJ, double *ESC, double *NORM)
 {
     const int T = m->n_lines;
     const double Rout = R[K - 1];
@@ -312,7 +330,7 @@ void lo_march_1d(const lo_molecule *m, int K, const double *R,
         double *phi = (double *)malloc(sizeof(double) * n_ch);
         lo_seg1d *segs = (lo_seg1d *)malloc(sizeof(lo_seg1d) * 2 * (K + 1));
 #pragma omp for schedule(static)
-        for (int j = 0; j < n_rays; j++) {
+        for (int j = 0; j < j_end; j++) {
             double p, A;
             lo_ray_1d(Rout, n_rays, ray_power, j, &p, &A);
             for (int t = 0; t < T; t++) {
@@ -395,16 +413,17 @@ void lo_line_off(const lo_molecule *m, int n_cells, const double *x, double cuto
     }
 }
 
-/* off: [line][cell] truncation mask of lo_line_off, or NULL (none). */
-int lo_se_solve_off(const lo_molecule *m, int n_cells, const double *n_h2,
-                    const double *t_kin, double t_bg, int ali,
-                    const double *SIJ, const double *ESC, const double *NORM,
-                    const double *S, const unsigned char *off, double *x_out)
+/* off: [line][cell] truncation mask of lo_line_off, or NULL (none).
+ * Solves cells [0, c_end) of the n_cells; the others are not written. */
+static int lo_se_solve_range(const lo_molecule *m, int n_cells, int c_end, const double *n_h2,
+                             const double *t_kin, double t_bg, int ali,
+                             const double *SIJ, const double *ESC, const double *NORM,
+                             const double *S, const unsigned char *off, double *x_out)
 {
     const int L = m->n_levels, T = m->n_lines;
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(+:bad)
-    for (int c = 0; c < n_cells; c++) {
+    for (int c = 0; c < c_end; c++) {
         double *R = (double *)calloc((size_t)L * L, sizeof(double)); /* R[i][j]: rate i -> j */
         double *M = (double *)calloc((size_t)L * L, sizeof(double));
         double *b = (double *)calloc(L, sizeof(double));
@@ -451,6 +470,14 @@ int lo_se_solve_off(const lo_molecule *m, int n_cells, const double *n_h2,
         free(R); free(M); free(b);
     }
     return bad;
+}
+
+int lo_se_solve_off(const lo_molecule *m, int n_cells, const double *n_h2,
+                    const double *t_kin, double t_bg, int ali,
+                    const double *SIJ, const double *ESC, const double *NORM,
+                    const double *S, const unsigned char *off, double *x_out)
+{
+    return lo_se_solve_range(m, n_cells, n_cells, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, off, x_out);
 }
 
 int lo_se_solve(const lo_molecule *m, int n_cells, const double *n_h2,
@@ -544,6 +571,67 @@ int lo_iterate_1d(const lo_molecule *m, int K, const double *R,
 {
     return lo_iterate_1d_cut(m, K, R, n_h2, t_kin, sigma_turb, abundance, v, n_ch, v_min, dv,
                              n_rays, ray_power, t_bg, ali, n_iter, 0.0, x, dtex);
+}
+
+/* Rays that cross shells 0 .. k_sub - 1: the rays whose tangent shell is
+ * below k_sub (impact parameters increase with j, so they are j < j_end). */
+int lo_sub_rays_1d(int K, const double *R, int n_rays, double ray_power, int k_sub)
+{
+    const double Rout = R[K - 1];
+    int j_end = 0;
+    for (int j = 0; j < n_rays; j++) {
+        double p, A;
+        lo_ray_1d(Rout, n_rays, ray_power, j, &p, &A);
+        if (lo_tangent_shell(K, R, p) < k_sub) j_end = j + 1;
+    }
+    return j_end;
+}
+
+/* ALI with sub-iterations on an inner region (Sect. 4 proposes updating the
+ * populations of optically thick regions more often than the rest; the
+ * scheme is our reading).  Each iteration is one full iteration (line
+ * parameters, ray simulation of all rays, equilibrium of every cell)
+ * followed by n_sub sub-iterations of the region of the k_sub innermost
+ * shells: line parameters from the current populations, a ray simulation of
+ * the rays that cross the region only (every ray that reaches a region cell,
+ * so the region's sums are complete), and the equilibrium of the region's
+ * cells only; the populations outside the region stay as the full
+ * iteration left them.  dtex[it] is the metric between the populations
+ * before and after the whole iteration. */
+int lo_iterate_1d_sub(const lo_molecule *m, int K, const double *R,
+                      const double *n_h2, const double *t_kin,
+                      const double *sigma_turb, const double *abundance,
+                      const double *v, int n_ch, double v_min, double dv,
+                      int n_rays, double ray_power, double t_bg, int ali, int n_iter,
+                      int n_sub, int k_sub, double *x, double *dtex)
+{
+    const int T = m->n_lines, L = m->n_levels;
+    double *Kp = (double *)malloc(sizeof(double) * T * K);
+    double *S = (double *)malloc(sizeof(double) * T * K);
+    double *SIJ = (double *)malloc(sizeof(double) * T * K);
+    double *ESC = (double *)malloc(sizeof(double) * T * K);
+    double *NORM = (double *)malloc(sizeof(double) * K);
+    double *xn = (double *)malloc(sizeof(double) * L * K);
+    double *x0 = (double *)malloc(sizeof(double) * L * K);
+    const int j_end = lo_sub_rays_1d(K, R, n_rays, ray_power, k_sub);
+    int bad = 0;
+    for (int it = 0; it < n_iter; it++) {
+        memcpy(x0, x, sizeof(double) * L * K);
+        lo_line_params(m, K, n_h2, abundance, dv, x, Kp, S);
+        lo_march_1d(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S, SIJ, ESC, NORM);
+        bad += lo_se_solve_off(m, K, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, NULL, xn);
+        memcpy(x, xn, sizeof(double) * L * K);
+        for (int q = 0; q < n_sub; q++) {
+            lo_line_params(m, K, n_h2, abundance, dv, x, Kp, S);
+            lo_march_1d_rays(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg,
+                             Kp, S, j_end, SIJ, ESC, NORM);
+            bad += lo_se_solve_range(m, K, k_sub, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, NULL, xn);
+            memcpy(x, xn, sizeof(double) * L * k_sub);     /* region cells only ([cell][level]) */
+        }
+        if (dtex) dtex[it] = lo_max_rel_dtex(m, K, x0, x);
+    }
+    free(Kp); free(S); free(SIJ); free(ESC); free(NORM); free(xn); free(x0);
+    return bad;
 }
 
 /* Emergent spectra of a 1D model (Sect. 2: final line-of-sight integration
