@@ -185,21 +185,29 @@ def march_1d(mol, model, Kp, S, n_levels=None):
     return SIJ, ESC, NORM
 
 
-def march_1d_rays(mol, model, Kp, S, j_end, n_levels=None):
-    """The ray simulation of rays j < j_end only (weights from all rays)."""
+def march_1d_sub(mol, model, Kp, S, k_sub, mode, Ib=None, n_levels=None):
+    """Ray simulation with the region of the k_sub innermost shells.
+    mode 0: all rays; returns (SIJ, ESC, NORM, Ib) with Ib[j][line][channel]
+    the intensity ray j carries into the region.  mode 1: the region's steps
+    of the rays that reach it, starting from Ib; returns (SIJ, ESC, NORM)."""
     lib = _load()
     M = _Mol(mol, n_levels)
     K = len(model["radius"])
     SIJ = np.zeros((M.T, K))
     ESC = np.zeros((M.T, K))
     NORM = np.zeros(K)
-    lib.lo_march_1d_rays(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["t_kin"])),
-                         _p(_f64(model["sigma_turb"])), _p(_f64(model["v"])),
-                         int(model["n_ch"]), ctypes.c_double(model["v_min"]),
-                         ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
-                         ctypes.c_double(model["t_bg"]), _p(_f64(Kp)), _p(_f64(S)), int(j_end),
-                         _p(SIJ), _p(ESC), _p(NORM))
-    return SIJ, ESC, NORM
+    j_end = sub_rays_1d(model, k_sub)
+    if mode == 0:
+        Ib = np.zeros((max(j_end, 1), M.T, int(model["n_ch"])))
+    else:
+        Ib = _f64(Ib)
+    lib.lo_march_1d_sub(M.ref, K, _p(_f64(model["radius"])), _p(_f64(model["t_kin"])),
+                        _p(_f64(model["sigma_turb"])), _p(_f64(model["v"])),
+                        int(model["n_ch"]), ctypes.c_double(model["v_min"]),
+                        ctypes.c_double(model["dv"]), int(model["n_rays"]), _ray_power(model),
+                        ctypes.c_double(model["t_bg"]), _p(_f64(Kp)), _p(_f64(S)), int(k_sub),
+                        int(mode), int(j_end), _p(Ib), _p(SIJ), _p(ESC), _p(NORM))
+    return (SIJ, ESC, NORM, Ib[:j_end]) if mode == 0 else (SIJ, ESC, NORM)
 
 
 def sub_rays_1d(model, k_sub):

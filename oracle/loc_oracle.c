@@ -281,13 +281,19 @@ void lo_weights_1d(int K, const double *R, int n_rays, double ray_power, double 
  * lo_step, and each step's contribution carries the weight
  * w = A_j s / W_c (so that sum(w) = 1 per cell).  Outputs SIJ, ESC
  * [line][cell] and NORM [cell], zeroed here. */
-/* The same ray simulation restricted to rays j < j_end (the weights W_c
- * still come from all n_rays rays). */
-void lo_march_1d_rays(const lo_molecule *m, int K, const double *R,
-                      const double *t_kin, const double *sigma_turb,
-                      const double *v, int n_ch, double v_min, double dv,
-                      int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
-                      int j_end, double *SIJ, double *ESC, double *NORM);
+/* The same ray simulation with a region of the k_sub innermost shells
+ * (weights W_c from all n_rays rays in every mode):
+ *   mode 0: all rays; each ray that reaches the region leaves in
+ *           Ib[j][line][channel] the intensity it carries into it (before its
+ *           first step inside the region);
+ *   mode 1: only the rays j < j_end that reach the region, only their steps
+ *           inside it, each starting from Ib[j]. */
+void lo_march_1d_sub(const lo_molecule *m, int K, const double *R,
+                     const double *t_kin, const double *sigma_turb,
+                     const double *v, int n_ch, double v_min, double dv,
+                     int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
+                     int k_sub, int mode, int j_end, double *Ib,
+                     double *SIJ, double *ESC, double *NORM);
 
 void lo_march_1d(const lo_molecule *m, int K, const double *R,
                  const double *t_kin, const double *sigma_turb,
@@ -295,16 +301,18 @@ void lo_march_1d(const lo_molecule *m, int K, const double *R,
                  int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
                  double *SIJ, double *ESC, double *NORM)
 {
-    lo_march_1d_rays(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S,
-                     n_rays, SIJ, ESC, NORM);
+    lo_march_1d_sub(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S,
+                    0, 0, n_rays, NULL, SIJ, ESC, NORM);
 }
 
-void lo_march_1d_rays(const lo_molecule *m, int K, const double *R,
-                      const double *t_kin, const double *sigma_turb,
-                      const double *v, int n_ch, double v_min, double dv,
-                      int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
-                      int j_end, double *SIJ, double *ESC, double *NORM)
+void lo_march_1d_sub(const lo_molecule *m, int K, const double *R,
+                     const double *t_kin, const double *sigma_turb,
+                     const double *v, int n_ch, double v_min, double dv,
+                     int n_rays, double ray_power, double t_bg, const double *Kp, const double *S,
+                     int k_sub, int mode, int j_end, double *Ib,
+                     double *SIJ, double *ESC, double *NORM)
 {
+    if (mode == 0) j_end = n_rays;
     const int T = m->n_lines;
     const double Rout = R[K - 1];
     double *W = (double *)malloc(sizeof(double) * K);
@@ -338,7 +346,18 @@ void lo_march_1d_rays(const lo_molecule *m, int K, const double *R,
                 for (int k = 0; k < n_ch; k++) I[t * n_ch + k] = nbg;
             }
             int n = lo_ray_segments_1d(K, R, p, segs);
-            for (int i = 0; i < n; i++) {
+            /* the ray's steps inside the region: the middle 2 (K - k_sub) fewer */
+            const int outer = (k_sub > 0) ? K - k_sub : 0;
+            const int reaches = (k_sub > 0) && (n > 2 * outer);
+            int i0 = 0, i1 = n;
+            if (mode == 1) {
+                i0 = outer;
+                i1 = n - outer;
+                memcpy(I, Ib + (size_t)j * T * n_ch, sizeof(double) * T * n_ch);
+            }
+            for (int i = i0; i < i1; i++) {
+                if (mode == 0 && reaches && Ib && i == outer)
+                    memcpy(Ib + (size_t)j * T * n_ch, I, sizeof(double) * T * n_ch);
                 const int c = segs[i].cell;
                 const double sig = lo_sigma(sigma_turb[c], t_kin[c], m->mass_amu);
                 lo_profile(n_ch, v_min, dv, v[c] * segs[i].cosv, sig, phi);
@@ -593,11 +612,13 @@ int lo_sub_rays_1d(int K, const double *R, int n_rays, double ray_power, int k_s
  * parameters, ray simulation of all rays, equilibrium of every cell)
  * followed by n_sub sub-iterations of the region of the k_sub innermost
  * shells: line parameters from the current populations, a ray simulation of
- * the rays that cross the region only (every ray that reaches a region cell,
- * so the region's sums are complete), and the equilibrium of the region's
- * cells only; the populations outside the region stay as the full
- * iteration left them.  dtex[it] is the metric between the populations
- * before and after the whole iteration. */
+ * the rays that reach the region (every ray that crosses a region cell, so
+ * the region's sums are complete) over their steps inside it, each ray
+ * starting with the intensity it carried into the region in the full
+ * iteration (the radiation entering the region is held), and the
+ * equilibrium of the region's cells only; the populations outside the region
+ * stay as the full iteration left them.  dtex[it] is the metric between the
+ * populations before and after the whole iteration. */
 int lo_iterate_1d_sub(const lo_molecule *m, int K, const double *R,
                       const double *n_h2, const double *t_kin,
                       const double *sigma_turb, const double *abundance,
@@ -614,23 +635,25 @@ int lo_iterate_1d_sub(const lo_molecule *m, int K, const double *R,
     double *xn = (double *)malloc(sizeof(double) * L * K);
     double *x0 = (double *)malloc(sizeof(double) * L * K);
     const int j_end = lo_sub_rays_1d(K, R, n_rays, ray_power, k_sub);
+    double *Ib = (double *)malloc(sizeof(double) * ((size_t)j_end + 1) * T * n_ch);
     int bad = 0;
     for (int it = 0; it < n_iter; it++) {
         memcpy(x0, x, sizeof(double) * L * K);
         lo_line_params(m, K, n_h2, abundance, dv, x, Kp, S);
-        lo_march_1d(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S, SIJ, ESC, NORM);
+        lo_march_1d_sub(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg, Kp, S,
+                        k_sub, 0, n_rays, Ib, SIJ, ESC, NORM);
         bad += lo_se_solve_off(m, K, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, NULL, xn);
         memcpy(x, xn, sizeof(double) * L * K);
         for (int q = 0; q < n_sub; q++) {
             lo_line_params(m, K, n_h2, abundance, dv, x, Kp, S);
-            lo_march_1d_rays(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg,
-                             Kp, S, j_end, SIJ, ESC, NORM);
+            lo_march_1d_sub(m, K, R, t_kin, sigma_turb, v, n_ch, v_min, dv, n_rays, ray_power, t_bg,
+                            Kp, S, k_sub, 1, j_end, Ib, SIJ, ESC, NORM);
             bad += lo_se_solve_range(m, K, k_sub, n_h2, t_kin, t_bg, ali, SIJ, ESC, NORM, S, NULL, xn);
             memcpy(x, xn, sizeof(double) * L * k_sub);     /* region cells only ([cell][level]) */
         }
         if (dtex) dtex[it] = lo_max_rel_dtex(m, K, x0, x);
     }
-    free(Kp); free(S); free(SIJ); free(ESC); free(NORM); free(xn); free(x0);
+    free(Kp); free(S); free(SIJ); free(ESC); free(NORM); free(xn); free(x0); free(Ib);
     return bad;
 }
 
