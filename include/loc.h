@@ -202,6 +202,20 @@ typedef struct loc_molecule_desc {
  *                 their accumulators (loc_radiation_buffers) before
  *                 loc_solve; loc_iterate with a range solves from that
  *                 share alone.  Ignored for 1D models.
+ *  sub_iters, sub_shells  1D models, loc_iterate: after every full ALI
+ *                 iteration, sub_iters sub-iterations of the region of the
+ *                 sub_shells innermost shells (Sect. 4 suggests updating
+ *                 optically thick regions more often): line parameters of
+ *                 the region, a ray simulation of the rays that reach it --
+ *                 only their steps inside it, from the intensity each ray
+ *                 carried into the region in the full iteration -- and the
+ *                 equilibrium of the region's cells; the populations outside
+ *                 the region are held.  max_iter and tol_tex count full
+ *                 iterations; the metric compares the populations before
+ *                 and after the whole iteration.  Whole rays are marched
+ *                 (steps_per_chunk is ignored); level_cutoff must be 0.
+ *                 Afterwards the accumulators hold the last sub-iteration's
+ *                 sums of the region.  0: none.
  */
 typedef struct loc_iter_opts {
     int max_iter;
@@ -214,6 +228,7 @@ typedef struct loc_iter_opts {
     int steps_per_chunk;
     double level_cutoff;
     int dir_begin, dir_end;
+    int sub_iters, sub_shells;
 } loc_iter_opts;
 
 /* Iteration report. */

@@ -63,6 +63,7 @@ batch_march_kernel(BatchSlot *slots, const int4 *items, const int *n_items, unsi
         if (!S->active) continue;
         const DevModel m = S->m;
         MarchArgs a0;
+        memset(&a0, 0, sizeof(a0));
         a0.per = S->per;
         a0.n_groups = S->n_groups;
         a0.window = window;

@@ -184,21 +184,21 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane)
     return v[0];
 }
 
-// Data of one ray step.
+// Data of one ray step.  The lines' parameters are spread over the lanes:
+// lane t < n_lines holds {K, S} of line t of the pass (one coalesced load
+// per step), the others {0, 0}; march_step broadcasts them by shuffle.
 template <int G>
 struct Step {
     long long cell;
     float s, w;          // path length (cm), weight of the step
     float vlos, inv;     // line-of-sight velocity, 1/(sqrt(2) sigma)
-    float2 ks[G];        // {K, S} of the lines of this pass
+    float2 kl;           // {K, S} of this lane's line
 };
 
 template <int G>
-__device__ __forceinline__ void load_lines(const DevModel &m, const MarchArgs &a, Step<G> &st)
+__device__ __forceinline__ void load_lines(const DevModel &m, const MarchArgs &a, Step<G> &st, int lane)
 {
-    const float2 *p = m.ks + st.cell * m.T + a.line0;
-#pragma unroll
-    for (int t = 0; t < G; t++) st.ks[t] = (t < a.n_lines) ? p[t] : make_float2(0.f, 0.f);
+    st.kl = (lane < a.n_lines) ? m.ks[st.cell * m.T + a.line0 + lane] : make_float2(0.f, 0.f);
 }
 
 // Channel coordinate offset u0 (the local line centre sits at channel -u0),
@@ -236,14 +236,10 @@ __device__ __forceinline__ float step_ks(float K, float s)
 // whose lines are all off in its cell is skipped outright by the warps that
 // do not sum NORM.
 template <int G>
-__device__ __forceinline__ bool lines_off(const DevModel &m, const MarchArgs &a, const Step<G> &st)
+__device__ __forceinline__ bool lines_off(const DevModel &m, const MarchArgs &a, const Step<G> &st, int lane)
 {
     if (!m.trunc || a.do_norm) return false;
-    bool off = true;
-#pragma unroll
-    for (int t = 0; t < G; t++)
-        off &= (t >= a.n_lines) | (__float_as_uint(st.ks[t].x) == 0x80000000u);
-    return off;
+    return __ballot_sync(kFull, lane < a.n_lines && __float_as_uint(st.kl.x) != 0x80000000u) == 0u;
 }
 
 // Lane of a warp that adds the step's NORM (lanes t < n_lines <= G add the
@@ -326,14 +322,8 @@ __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchA
     const float phi_c = (lane < W) ? ((b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1)))
                                    : 0.f;
     // line parameters: lane t holds line t's K s and S
-    float my_k = 1e-20f, my_s = 0.f;
-#pragma unroll
-    for (int t = 0; t < G; t++) {
-        if (lane == t) {
-            my_k = step_ks(st.ks[t].x, st.s);
-            my_s = st.ks[t].y;
-        }
-    }
+    const float my_k = (lane < G) ? step_ks(st.kl.x, st.s) : 1e-20f;
+    const float my_s = (lane < G) ? st.kl.y : 0.f;
     const int tl = lane / Wp, kk = lane - tl * Wp;
     float g_sij = 0.f, g_esc = 0.f;
     for (int base = 0; base < a.n_lines; base += P) {
@@ -377,25 +367,23 @@ template <int G, int ACC>
 __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
                                           const Step<G> &st, int lane, MarchState &pend)
 {
-    if (lines_off<G>(m, a, st)) return 0;
+    if (lines_off<G>(m, a, st, lane)) return 0;
     const int nch = m.n_ch;
     if (a.count) {
         int on = a.n_lines;
-        if (m.trunc) {
-            on = 0;
-#pragma unroll
-            for (int t = 0; t < G; t++) on += (t < a.n_lines) & (__float_as_uint(st.ks[t].x) != 0x80000000u);
-        }
+        if (m.trunc)
+            on = __popc(__ballot_sync(kFull, lane < a.n_lines && __float_as_uint(st.kl.x) != 0x80000000u));
         pend.nom += on;
     }
     float u0, db;
     int klo, khi;
     step_window(m, a, st, u0, db, klo, khi);
     if (khi - klo <= 16) return march_step_packed<G, ACC>(m, a, I, st, lane, klo, khi, u0, db, pend);
-    float Ks[G], sij[G], esc[G];
+    float Ks[G], Sv[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
-        Ks[t] = step_ks(st.ks[t].x, st.s);
+        Ks[t] = step_ks(__shfl_sync(kFull, st.kl.x, t), st.s);
+        Sv[t] = __shfl_sync(kFull, st.kl.y, t);
         sij[t] = 0.f;
         esc[t] = 0.f;
     }
@@ -421,7 +409,7 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
                     const float iv = ip[t * nch];
                     sij[t] = fmaf(iv, tm, sij[t]);
                     esc[t] += tm;
-                    ip[t * nch] = fmaf(st.ks[t].y - iv, tm, iv);
+                    ip[t * nch] = fmaf(Sv[t] - iv, tm, iv);
                 }
             } else {
 #pragma unroll
@@ -431,7 +419,7 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
                         const float iv = ip[t * nch];
                         sij[t] = fmaf(iv, tm, sij[t]);
                         esc[t] += tm;
-                        ip[t * nch] = fmaf(st.ks[t].y - iv, tm, iv);
+                        ip[t * nch] = fmaf(Sv[t] - iv, tm, iv);
                     }
                 }
             }
@@ -525,7 +513,7 @@ __device__ __forceinline__ long long walk_steps1d(const DevModel &m, const March
         st.vlos = __shfl_sync(kFull, rec.vlos, r);
         st.w = __shfl_sync(kFull, rec.w, r);
         st.inv = m.inv_s2sig[st.cell];
-        load_lines<G>(m, a, st);
+        load_lines<G>(m, a, st, lane);
     };
     long long nw = 0;
     Step<G> cur, nxt;
@@ -542,16 +530,43 @@ __device__ __forceinline__ long long walk_steps1d(const DevModel &m, const March
 
 // One 1D ray (equidistant ray j) through all its steps for the warp's line
 // group.  Returns the number of channels computed.
+// Copies the warp's intensities of its line group to (to_store) or from the
+// region-boundary buffer of ray j.
+__device__ __forceinline__ void sub_boundary(const DevModel &m, const MarchArgs &a, float *I, int j, int lane,
+                                             bool to_store)
+{
+    float *b = a.sub_I + ((size_t)j * m.T + a.line0) * m.n_ch;
+    for (int i = lane; i < a.n_lines * m.n_ch; i += 32) {
+        if (to_store) b[i] = I[i];
+        else I[i] = b[i];
+    }
+    __syncwarp();
+}
+
 template <int G, int ACC>
 __device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchArgs &a, float *I,
                                                  int j, int lane)
 {
-    init_ray<G>(m, a, I, lane);
     const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
     MarchState pend = march_state();
-    const long long nw = walk_steps1d<G>(m, a, s0, n, lane, [&](const Step<G> &st) {
-        return (long long)march_step<G, ACC>(m, a, I, st, lane, pend);
-    });
+    auto fn = [&](const Step<G> &st) { return (long long)march_step<G, ACC>(m, a, I, st, lane, pend); };
+    long long nw = 0;
+    const int outer = m.K - a.sub_k;                  // steps before the region (sub_k > 0)
+    if (a.sub_k > 0 && a.sub_mode == 1) {
+        // a sub-iteration: the region's steps of the ray, from the intensity
+        // the full march left at the region's boundary
+        sub_boundary(m, a, I, j, lane, false);
+        nw = walk_steps1d<G>(m, a, s0 + outer, n - 2 * outer, lane, fn);
+    } else if (a.sub_k > 0 && a.sub_I && n > 2 * outer) {
+        // full march of a ray that reaches the region: keep its intensity there
+        init_ray<G>(m, a, I, lane);
+        nw = walk_steps1d<G>(m, a, s0, outer, lane, fn);
+        sub_boundary(m, a, I, j, lane, true);
+        nw += walk_steps1d<G>(m, a, s0 + outer, n - outer, lane, fn);
+    } else {
+        init_ray<G>(m, a, I, lane);
+        nw = walk_steps1d<G>(m, a, s0, n, lane, fn);
+    }
     march_state_end<ACC>(m, a, pend, lane);
     return nw;
 }
@@ -567,15 +582,18 @@ template <int G>
 __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &a, float *A, float *B,
                                             const Step<G> &st, int lane, int tlo, int thi)
 {
-    if (lines_off<G>(m, a, st)) return;                   // identity map
+    if (lines_off<G>(m, a, st, lane)) return;             // identity map
     float u0, db;
     int klo, khi;
     step_window(m, a, st, u0, db, klo, khi);
     klo = max(klo, tlo);
     khi = min(khi, thi);
-    float Ks[G];
+    float Ks[G], Sv[G];
 #pragma unroll
-    for (int t = 0; t < G; t++) Ks[t] = step_ks(st.ks[t].x, st.s);
+    for (int t = 0; t < G; t++) {
+        Ks[t] = step_ks(__shfl_sync(kFull, st.kl.x, t), st.s);
+        Sv[t] = __shfl_sync(kFull, st.kl.y, t);
+    }
     const bool full = (a.n_lines == G);
     const int tile = a.tile;
     for (int base = klo; base < khi; base += 31) {
@@ -593,7 +611,7 @@ __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &
                     const int o = t * tile + k - tlo;
                     const float av = A[o], bv = B[o];
                     A[o] = fmaf(-av, tm, av);
-                    B[o] = fmaf(st.ks[t].y - bv, tm, bv);
+                    B[o] = fmaf(Sv[t] - bv, tm, bv);
                 }
             }
         }

@@ -5,7 +5,7 @@
 namespace loc {
 
 template <int G, int ACC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) march1d_kernel(DevModel m, MarchArgs a0)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 11 ? 5 : 3) march1d_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
@@ -188,9 +188,9 @@ __global__ void march1d_scan_kernel(DevModel m, MarchArgs a)
     }
 }
 
-// registers capped at 128 (4 blocks per SM) up to 11 lines per warp
+// registers capped for 5 blocks per SM up to 11 lines per warp
 template <int G, int ACC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 11 ? 4 : 3) march1d_run_kernel(DevModel m, MarchArgs a0)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 11 ? 5 : 3) march1d_run_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;

@@ -5,8 +5,9 @@
 namespace loc {
 
 // 3D regular grid: one warp per (direction, root line, line group).
+// registers capped for 4 blocks per SM up to 8 lines per warp, 3 above
 template <int G, int ACC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m, MarchArgs a0)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 8 ? 4 : 3) march3d_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) march3d_kernel(DevModel m
         st.inv = cv.w;
         st.s = (float)(int)dz * D.unit;             // dz <= one cell = 2^24 units
         st.w = (float)(int)dz * wscale;
-        load_lines<G>(m, a, st);
+        load_lines<G>(m, a, st, lane);
     };
     long long nw = 0;
     Step<G> cur, nxt;

@@ -412,7 +412,7 @@ __device__ void oct_traverse(const DevModel &m, const MarchArgs &a, const OctGeo
                 st.inv = cv.w;
                 st.s = (float)(int)dz * g.D.unit;       // dz <= one leaf <= 2^24 units
                 st.w = oct_weight(dz, Lc, wscale);
-                load_lines<G>(m, a, st);
+                load_lines<G>(m, a, st, lane);
                 nw += (long long)march_step<G, ACC>(m, a, I, st, lane, pend) * a.n_lines;
                 __syncwarp();
             } else {
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) record_octree_kernel(D
 // ----------------------------------------------------------------------------
 template <int G>
 __device__ __forceinline__ void replay_load(const DevModel &m, const MarchArgs &a, const Dir3D &D,
-                                            float wscale, unsigned long long x, Step<G> &st)
+                                            float wscale, unsigned long long x, Step<G> &st, int lane)
 {
     const int leaf = (int)(unsigned)(x & 0xffffffffull);
     const long long dz = (long long)((x >> 32) & 0x1ffffffull);
@@ -608,7 +608,7 @@ __device__ __forceinline__ void replay_load(const DevModel &m, const MarchArgs &
     st.inv = cv.w;
     st.s = (float)(int)dz * D.unit;
     st.w = oct_weight(dz, Lc, wscale);
-    load_lines<G>(m, a, st);
+    load_lines<G>(m, a, st, lane);
 }
 
 template <int G, int ACC>
@@ -638,9 +638,9 @@ __device__ long long replay_family(const DevModel &m, const MarchArgs &a, const 
         const unsigned long long y = (r < 31) ? y1 : y2;
         const unsigned type = (unsigned)(x >> 61);
         if (type == kRecStep) {
-            if (!pre) replay_load<G>(m, a, D, wscale, x, cur);
+            if (!pre) replay_load<G>(m, a, D, wscale, x, cur, lane);
             const bool nstep = (q + 1 < r1) && ((unsigned)(y >> 61) == kRecStep);
-            if (nstep) replay_load<G>(m, a, D, wscale, y, nxt);
+            if (nstep) replay_load<G>(m, a, D, wscale, y, nxt, lane);
             nw += (long long)march_step<G, ACC>(m, a, I, cur, lane, pend) * a.n_lines;
             __syncwarp();
             if (nstep) cur = nxt;
@@ -661,10 +661,10 @@ __device__ long long replay_family(const DevModel &m, const MarchArgs &a, const 
     return nw;
 }
 
-// registers capped so that 4 blocks (16 warps) fit per SM, 5 for small line
-// groups
+// registers capped so that 5 blocks (20 warps) fit per SM, 4 for the
+// largest line groups
 template <int G, int ACC>
-__global__ void __launch_bounds__(kOctWarpsPerBlock * 32, G <= 6 ? 5 : 4) replay_octree_kernel(DevModel m, MarchArgs a0,
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32, G <= 11 ? 5 : 4) replay_octree_kernel(DevModel m, MarchArgs a0,
                                                                                 unsigned *counter)
 {
     extern __shared__ float smem[];

@@ -285,6 +285,35 @@ loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st
     return LOC_OK;
 }
 
+// Convergence metric between the populations x0 and m.x: max over cells
+// and over lines whose upper level now holds >= 1e-6 of |dT_ex| / |T_ex|,
+// as the solve computes it (one thread per (cell, line)).
+__global__ void dtex_kernel(DevModel m, const double *x0)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float d = 0.f;
+    if (idx < (long long)m.T * m.n_cells) {
+        const long long c = idx / m.T;
+        const int t = (int)(idx - c * m.T);
+        const double *xn = m.x + c * m.L;
+        if (!(xn[m.line_u[t]] < 1e-6)) {
+            const double a = tex_of(m, t, x0 + c * m.L);
+            if (a != 0.0) d = (float)(fabs(tex_of(m, t, xn) - a) / fabs(a));
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, off));
+    if ((threadIdx.x & 31) == 0 && d > 0.f) atomicMax(m.dtex_bits, __float_as_uint(d));
+}
+
+loc_status launch_dtex(const DevModel &m, const double *x0, cudaStream_t st)
+{
+    const long long n = (long long)m.T * m.n_cells;
+    dtex_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, x0);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
 // accumulators -> FP64 arrays (diagnostics)
 __global__ void acc_to_f64_kernel(DevModel m, int fp64_acc, double *sij, double *esc, double *norm)
 {

@@ -64,6 +64,14 @@ struct loc_model {
     std::vector<void *> oct_mem;
     long long path_records = 0;      // octree: recorded path records (0: the march walks the tree)
     std::vector<void *> path_mem;
+    // 1D sub-iterations (set for the duration of a loc_iterate call)
+    int sub_k = 0;                   // region: the sub_k innermost shells (0: none)
+    int sub_mode = 0;                // 0: full march storing sub_I, 1: region march
+    int sub_rays = 0;                // rays that reach the region
+    float *sub_I = nullptr;          // [sub_rays][T][n_ch] intensities at the region's boundary
+    double *sub_x0 = nullptr;        // populations at the start of the iteration
+    size_t sub_bytes = 0;
+    std::vector<void *> sub_mem;
 };
 
 static void *dev_alloc(loc_model *m, size_t bytes, std::vector<void *> &owner)
@@ -534,6 +542,8 @@ static loc_status check_opts(const loc_iter_opts *o)
     CHECK(o->profile == 0 || o->profile == 1, "profile must be 0 or 1");
     CHECK(o->level_cutoff >= 0.0 && o->level_cutoff <= 1e-6, "level_cutoff must be in [0, 1e-6]");
     CHECK(o->dir_begin >= 0 && o->dir_end >= 0, "direction range must be >= 0");
+    CHECK(o->sub_iters >= 0 && o->sub_iters <= 1000, "sub_iters must be in [0, 1000]");
+    CHECK(o->sub_iters == 0 || o->level_cutoff == 0.0, "sub-iterations and level_cutoff do not combine");
     return LOC_OK;
 }
 
@@ -570,6 +580,7 @@ static int steps_per_run(const loc_model *m, const loc_iter_opts *o, int per)
 {
     const DevModel &D = m->d;
     if (D.geometry != LOC_SHELLS_1D) return 0;
+    if (m->sub_k > 0) return 0;                  // sub-iterations march whole rays
     int c = o->steps_per_chunk != 0 ? o->steps_per_chunk : m->tuned_chunk;
     if (c < 0) return 0;
     if (c > 0) return c;
@@ -697,8 +708,15 @@ static loc_status march_impl(loc_model *m, const loc_iter_opts *o, bool zeroed =
     a.fp64_acc = fp64;
     a.comp = o->precision == LOC_FP32_MARCH;
     a.count = o->profile;
+    a.sub_k = m->sub_k;
+    a.sub_mode = m->sub_mode;
+    a.sub_I = m->sub_I;
     if (run > 0) {
         if (a.n_chunks > 0) TRY(launch_march1d_chunked(D, a, m->st));
+    } else if (m->sub_k > 0 && m->sub_mode == 1) {
+        DevModel R = D;                          // the rays that reach the region
+        R.n_rays = m->sub_rays;
+        if (R.n_rays > 0) TRY(launch_march(R, a, m->st));
     } else {
         TRY(launch_march(D, a, m->st));
     }
@@ -789,6 +807,63 @@ loc_status loc_march(loc_model *m, const loc_iter_opts *o)
     return octree_status(m);
 }
 
+// Sub-iterations (1D): the region is the sub_shells innermost shells; the
+// rays that reach it are those whose step list is longer than the 2 (K -
+// sub_shells) steps outside it (impact parameters grow with the ray index,
+// so they are the first sub_rays rays).  Buffers for the intensities at the
+// region's boundary and for the populations at the start of an iteration.
+static loc_status sub_setup(loc_model *m, const loc_iter_opts *o)
+{
+    DevModel &D = m->d;
+    CHECK(D.geometry == LOC_SHELLS_1D, "sub-iterations need a 1D model");
+    CHECK(o->sub_shells >= 1 && o->sub_shells <= D.K, "sub_shells must be in [1, %d]", D.K);
+    const int outer = D.K - o->sub_shells;
+    int rays = 0;
+    for (int j = 0; j < D.n_rays; j++)
+        if (m->ray_off_h[j + 1] - m->ray_off_h[j] > 2 * outer) rays = j + 1;
+    const size_t bI = sizeof(float) * (size_t)std::max(rays, 1) * D.T * D.n_ch;
+    const size_t bx = sizeof(double) * (size_t)D.n_cells * D.L;
+    if (bI + bx > m->sub_bytes) {
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        dev_free_all(m, m->sub_mem);
+        m->sub_bytes = 0;
+        m->sub_I = (float *)dev_alloc(m, bI, m->sub_mem);
+        m->sub_x0 = (double *)dev_alloc(m, bx, m->sub_mem);
+        if (!m->sub_I || !m->sub_x0) { set_error("device allocation for sub-iterations failed"); return LOC_ENOMEM; }
+        m->sub_bytes = bI + bx;
+    }
+    m->sub_k = o->sub_shells;
+    m->sub_rays = rays;
+    m->sub_mode = 0;
+    return LOC_OK;
+}
+
+// n_sub sub-iterations of the region after a full iteration: line
+// parameters of the region's cells (accumulators cleared), the region's
+// steps of the rays that reach it from the intensities stored at its
+// boundary, the equilibrium of the region's cells, whose new populations
+// replace the old ones (the cells outside keep theirs).
+static loc_status sub_iterations(loc_model *m, const loc_iter_opts *o)
+{
+    DevModel &D = m->d;
+    DevModel R = D;
+    R.n_cells = m->sub_k;
+    const int fp64 = o->precision == LOC_FP64_ACC;
+    for (int q = 0; q < o->sub_iters; q++) {
+        TRY(launch_line_params(R, m->st, fp64 ? 2 : 1, 0.0));
+        m->sub_mode = 1;
+        const loc_status st = march_impl(m, o, true);
+        m->sub_mode = 0;
+        TRY(st);
+        R.x = D.x;
+        R.x_new = D.x_new;
+        TRY(launch_se(R, o->ali, fp64, m->st, 0, 0, 0.0));
+        LOC_CUDA_TRY(cudaMemcpyAsync(D.x, D.x_new, sizeof(double) * (size_t)m->sub_k * D.L,
+                                     cudaMemcpyDeviceToDevice, m->st));
+    }
+    return LOC_OK;
+}
+
 loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
 {
     if (!m) { set_error("NULL model"); return LOC_EINVAL; }
@@ -817,15 +892,19 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     int it = 0;
     float dtex = 0.f;
     bool converged = false;
-    const bool fuse = !(o->tol_tex > 0.0);
+    const bool sub = o->sub_iters > 0;
+    if (sub) TRY(sub_setup(m, o));
+    const bool fuse = !(o->tol_tex > 0.0) && !sub;
     D.trunc = o->level_cutoff > 0.0 ? 1 : 0;           // reset after the loop on every path
     loc_status st = LOC_OK;
     // NVTX ranges mark the host-side phases of every iteration for timeline
     // tools (no cost without an attached tool)
     nvtxRangePushA("loc_iterate");
     for (it = 0; it < o->max_iter; it++) {
-        const size_t b = 4 * (size_t)it;
+        const size_t b = 5 * (size_t)it;
         if (mark(b) != cudaSuccess) { st = LOC_ECUDA; break; }
+        if (sub && cudaMemcpyAsync(m->sub_x0, D.x, sizeof(double) * D.n_cells * D.L, cudaMemcpyDeviceToDevice,
+                                   m->st) != cudaSuccess) { st = LOC_ECUDA; break; }
         // with a fixed iteration count (no tolerance) the first iteration's
         // line parameters (and cleared accumulators) come from their own
         // launch and every later iteration's from the previous iteration's
@@ -850,11 +929,23 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
         }
         const int next = (fuse && it < o->max_iter - 1) ? 1 : 0;
         nvtxRangePushA("statistical equilibrium");
-        st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st, want, next, o->level_cutoff);
+        st = launch_se(D, o->ali, o->precision == LOC_FP64_ACC, m->st, sub ? 0 : want, next, o->level_cutoff);
         nvtxRangePop();
         if (st != LOC_OK) break;
         if (mark(b + 3) != cudaSuccess) { st = LOC_ECUDA; break; }
         std::swap(D.x, D.x_new);
+        if (sub) {
+            nvtxRangePushA("sub-iterations");
+            st = sub_iterations(m, o);
+            if (st == LOC_OK && want) {
+                // the metric of the whole iteration: populations before and after
+                if (cudaMemsetAsync(D.dtex_bits, 0, sizeof(unsigned), m->st) != cudaSuccess) st = LOC_ECUDA;
+                else st = launch_dtex(D, m->sub_x0, m->st);
+            }
+            nvtxRangePop();
+            if (st != LOC_OK) break;
+        }
+        if (mark(b + 4) != cudaSuccess) { st = LOC_ECUDA; break; }
         if (o->tol_tex > 0.0 || it == o->max_iter - 1) {
             unsigned bits = 0;
             if (cudaMemcpyAsync(&bits, D.dtex_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
@@ -869,6 +960,8 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     }
     nvtxRangePop();
     D.trunc = 0;
+    m->sub_k = 0;
+    m->sub_mode = 0;
     if (st == LOC_ECUDA && g_err[0] == 0) set_error("CUDA error in the iteration: %s", cudaGetErrorString(cudaGetLastError()));
     cudaEventRecord(e1, m->st);
     cudaError_t ce = cudaEventSynchronize(e1);
@@ -876,12 +969,15 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
     cudaEventElapsedTime(&ms, e0, e1);
     double t_par = 0.0, t_mar = 0.0, t_se = 0.0;
     if (prof && st == LOC_OK && ce == cudaSuccess) {
-        for (size_t b = 0; b + 3 < ev.size() && b / 4 < (size_t)it; b += 4) {
-            float a = 0.f, c = 0.f, d = 0.f;
+        // sub-iterations (line parameters, march and solve of the region)
+        // count as march time
+        for (size_t b = 0; b + 4 < ev.size() && b / 5 < (size_t)it; b += 5) {
+            float a = 0.f, c = 0.f, d = 0.f, e = 0.f;
             cudaEventElapsedTime(&a, ev[b], ev[b + 1]);
             cudaEventElapsedTime(&c, ev[b + 1], ev[b + 2]);
             cudaEventElapsedTime(&d, ev[b + 2], ev[b + 3]);
-            t_par += a; t_mar += c; t_se += d;
+            cudaEventElapsedTime(&e, ev[b + 3], ev[b + 4]);
+            t_par += a; t_mar += c + e; t_se += d;
         }
     }
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -1230,6 +1326,7 @@ void loc_destroy(loc_model *m)
     cudaStreamSynchronize(m->st);
     dev_free_all(m, m->oct_mem);
     dev_free_all(m, m->path_mem);
+    dev_free_all(m, m->sub_mem);
     dev_free_all(m, m->run_mem);
     dev_free_all(m, m->run_ab_mem);
     dev_free_all(m, m->mol_mem);

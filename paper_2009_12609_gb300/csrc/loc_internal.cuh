@@ -137,6 +137,12 @@ struct MarchArgs {
     int2 *run_rng;          // [n_chunks] channels [lo, hi) the run's step windows touch
     int tile;               // channels per shared-memory tile of the run maps (>= every run's union)
     int dir0, dir1;         // 3D: the march covers directions [dir0, dir1) of the model's table
+    // 1D sub-iterations of the sub_k innermost shells: the rays j < n_rays
+    // reach them, and the intensity a ray carries into them (at step
+    // K - sub_k of its list) is kept in sub_I[j][line][channel]
+    int sub_k;              // 0: none
+    int sub_mode;           // 0: full march, storing sub_I; 1: march the region's steps from sub_I
+    float *sub_I;
 };
 
 // ----------------------------------------------------------------------------
@@ -223,6 +229,7 @@ loc_status launch_lte(const DevModel &m, cudaStream_t st);
 loc_status launch_coll_rates(const DevModel &m, double2 *out, cudaStream_t st);
 loc_status launch_bg(const DevModel &m, cudaStream_t st);
 loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st);
+loc_status launch_dtex(const DevModel &m, const double *x0, cudaStream_t st);
 loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p, float4 *rec,
                             int *nsteps, float *T_dev, cudaStream_t st);
 loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,

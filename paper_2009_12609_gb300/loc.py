@@ -74,7 +74,7 @@ class loc_iter_opts(ctypes.Structure):
                 ("lines_per_pass", ctypes.c_int), ("window_sigmas", ctypes.c_double),
                 ("profile", ctypes.c_int), ("steps_per_chunk", ctypes.c_int),
                 ("level_cutoff", ctypes.c_double), ("dir_begin", ctypes.c_int),
-                ("dir_end", ctypes.c_int)]
+                ("dir_end", ctypes.c_int), ("sub_iters", ctypes.c_int), ("sub_shells", ctypes.c_int)]
 
 
 class loc_iter_report(ctypes.Structure):
@@ -304,12 +304,12 @@ def molecule_desc(mol, keep, n_levels=None):
 
 def iter_opts(max_iter=1, tol_tex=0.0, ali=True, precision="fp32", lines_per_pass=0,
               window_sigmas=0.0, profile=False, steps_per_chunk=0, level_cutoff=0.0,
-              dir_range=(0, 0)):
+              dir_range=(0, 0), sub_iters=0, sub_shells=0):
     prec = {"fp32": LOC_FP32_MARCH, "fp64acc": LOC_FP64_ACC, "fp32plain": LOC_FP32_PLAIN}[precision]
     return loc_iter_opts(int(max_iter), float(tol_tex), int(bool(ali)), prec,
                          int(lines_per_pass), float(window_sigmas), int(bool(profile)),
                          int(steps_per_chunk), float(level_cutoff), int(dir_range[0]),
-                         int(dir_range[1]))
+                         int(dir_range[1]), int(sub_iters), int(sub_shells))
 
 
 # --------------------------------------------------------------------------
