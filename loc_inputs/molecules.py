@@ -83,3 +83,22 @@ def rotor_molecule(n_levels=12, B_hz=57.6e9, mu_debye=0.11, mass_amu=28.0,
         coll_l=cl,
         coll_k=ck,
     )
+
+
+def with_hyperfine(mol, line=0, offsets_kms=(-1.1, 0.0, 0.7), strengths=(0.2, 0.5, 0.3)):
+    """The molecule with hyperfine structure on one line: components at
+    velocity offsets (km/s) with relative strengths (normalised to sum 1),
+    LTE among them; the other lines keep the plain profile.  Synthetic
+    values (the paper's examples use NH3 and HCN data, not available here).
+    Adds hf_n[T] (components per line, 0 = plain), hf_v (cm/s) and hf_w,
+    concatenated in line order."""
+    T = len(mol["line_nu"])
+    w = np.asarray(strengths, dtype=np.float64)
+    out = dict(mol)
+    n = np.zeros(T, dtype=np.int32)
+    n[line] = len(offsets_kms)
+    out["hf_n"] = n
+    out["hf_v"] = np.asarray(offsets_kms, dtype=np.float64) * 1.0e5
+    out["hf_w"] = w / w.sum()
+    out["name"] = mol["name"] + "+hf"
+    return out

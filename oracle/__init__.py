@@ -39,7 +39,8 @@ class _Molecule(ctypes.Structure):
                 ("n_coll", ctypes.c_int),
                 ("energy_K", _d), ("g", _d), ("mass_amu", ctypes.c_double),
                 ("line_u", _i), ("line_l", _i), ("line_A", _d), ("line_nu", _d),
-                ("coll_u", _i), ("coll_l", _i), ("coll_k", _d)]
+                ("coll_u", _i), ("coll_l", _i), ("coll_k", _d),
+                ("hf_off", _i), ("hf_v", _d), ("hf_w", _d)]
 
 
 def _load():
@@ -90,6 +91,19 @@ class _Mol:
         self.arrs.update(coll_u=np.ascontiguousarray(cu[keepc]),
                          coll_l=np.ascontiguousarray(cl[keepc]),
                          coll_k=_f64(np.asarray(mol["coll_k"])[keepc]))
+        # hyperfine components of the kept lines (hf_n per line, offsets and
+        # strengths concatenated in line order)
+        hf = None
+        if mol.get("hf_n") is not None:
+            n = np.asarray(mol["hf_n"], np.int64)
+            off = np.concatenate([[0], np.cumsum(n)])
+            idx = np.concatenate([np.arange(off[t], off[t + 1]) for t in np.flatnonzero(keep)] + [[]])
+            idx = idx.astype(np.int64)
+            kn = n[keep]
+            self.arrs.update(hf_off=np.ascontiguousarray(np.concatenate([[0], np.cumsum(kn)]), np.int32),
+                             hf_v=_f64(np.asarray(mol["hf_v"], np.float64)[idx]),
+                             hf_w=_f64(np.asarray(mol["hf_w"], np.float64)[idx]))
+            hf = self.arrs
         a = self.arrs
         self.L = L
         self.T = len(a["line_u"])
@@ -97,7 +111,9 @@ class _Mol:
         self.s = _Molecule(L, self.T, len(a["coll_u"]), _p(a["energy_K"]), _p(a["g"]),
                            float(mol["mass_amu"]), _p(a["line_u"]), _p(a["line_l"]),
                            _p(a["line_A"]), _p(a["line_nu"]), _p(a["coll_u"]),
-                           _p(a["coll_l"]), _p(a["coll_k"]))
+                           _p(a["coll_l"]), _p(a["coll_k"]),
+                           _p(hf["hf_off"]) if hf else None, _p(hf["hf_v"]) if hf else None,
+                           _p(hf["hf_w"]) if hf else None)
 
     @property
     def ref(self):

@@ -52,6 +52,12 @@ typedef struct {
     const double *line_A, *line_nu;
     const int *coll_u, *coll_l;
     const double *coll_k;
+    /* hyperfine components of the lines (1D, Sect. 2.1), or hf_off = NULL:
+     * line t's components are hf_off[t] .. hf_off[t+1]-1, each a velocity
+     * offset hf_v (cm/s) and a relative strength hf_w (summing to 1); a line
+     * with no components has the plain profile */
+    const int *hf_off;
+    const double *hf_v, *hf_w;
 } lo_molecule;
 
 /* Background occupation number of the cosmic background at temperature
@@ -110,6 +116,28 @@ void lo_profile(int n_ch, double v_min, double dv, double v_los, double sigma,
     }
 }
 
+/* Profile of line t with hyperfine structure in LTE between its
+ * components (Sect. 2.1; the relative populations of the components are
+ * fixed, so the line is one transition whose profile is the
+ * strength-weighted sum of the component profiles, each Doppler-shifted by
+ * its velocity offset: a component at offset v_c appears at channel
+ * velocity v_c - v_los).  phi0 is the unshifted profile; lines without
+ * components take it as it is. */
+static void lo_line_profile(const lo_molecule *m, int t, int n_ch, double v_min, double dv,
+                            double v_los, double sigma, const double *phi0, double *phi_t, double *tmp)
+{
+    const int c0 = m->hf_off ? m->hf_off[t] : 0, c1 = m->hf_off ? m->hf_off[t + 1] : 0;
+    if (c1 == c0) {
+        memcpy(phi_t, phi0, sizeof(double) * n_ch);
+        return;
+    }
+    for (int k = 0; k < n_ch; k++) phi_t[k] = 0.0;
+    for (int c = c0; c < c1; c++) {
+        lo_profile(n_ch, v_min, dv, v_los - m->hf_v[c], sigma, tmp);
+        for (int k = 0; k < n_ch; k++) phi_t[k] += m->hf_w[c] * tmp[k];
+    }
+}
+
 /* Total 1D line width: sigma^2 = sigma_turb^2 + k T / m (thermal plus
  * micro-turbulence; Sect. 3.3.1 counts thermal broadening in the width). */
 static double lo_sigma(double sigma_turb, double t_kin, double mass_amu)
@@ -160,10 +188,25 @@ void lo_line_params(const lo_molecule *m, int n_cells, const double *n_h2,
 /* the local term that ALI drops, Sect. 2), and then                         */
 /*   I <- I e^-tau + S (1 - e^-tau)                       (Eq. 3).           */
 /* ------------------------------------------------------------------------ */
+static void lo_step_lines(int n_lines, int n_ch, int n_cells, int cell,
+                          const double *phi, const double *phi_lines, double s, double w,
+                          const double *Kp, const double *S, double *I,
+                          double *sij, double *esc, double *norm);
+
 static void lo_step(int n_lines, int n_ch, int n_cells, int cell,
                     const double *phi, double s, double w,
                     const double *Kp, const double *S, double *I,
                     double *sij, double *esc, double *norm)
+{
+    lo_step_lines(n_lines, n_ch, n_cells, cell, phi, NULL, s, w, Kp, S, I, sij, esc, norm);
+}
+
+/* phi_lines: [n_lines][n_ch] per-line profiles (hyperfine), or NULL: every
+ * line has phi.  NORM always sums the plain profile phi. */
+static void lo_step_lines(int n_lines, int n_ch, int n_cells, int cell,
+                          const double *phi, const double *phi_lines, double s, double w,
+                          const double *Kp, const double *S, double *I,
+                          double *sij, double *esc, double *norm)
 {
     if (norm) {
         double sp = 0.0;
@@ -173,14 +216,15 @@ static void lo_step(int n_lines, int n_ch, int n_cells, int cell,
     for (int t = 0; t < n_lines; t++) {
         const size_t o = (size_t)t * n_cells + cell;
         const double kp = Kp[o], src = S[o];
+        const double *ph = phi_lines ? phi_lines + (size_t)t * n_ch : phi;
         double a_sij = 0.0, a_esc = 0.0;
         double *It = I + (size_t)t * n_ch;
         for (int k = 0; k < n_ch; k++) {
-            const double tau = kp * phi[k] * s;
+            const double tau = kp * ph[k] * s;
             const double one_m_e = -expm1(-tau);        /* 1 - e^-tau */
             const double f = (fabs(tau) < 1e-12) ? 1.0 - 0.5 * tau : one_m_e / tau;
-            a_sij += phi[k] * It[k] * f;
-            a_esc += phi[k] * f;
+            a_sij += ph[k] * It[k] * f;
+            a_esc += ph[k] * f;
             It[k] = It[k] * (1.0 - one_m_e) + src * one_m_e;
         }
         if (sij) {
@@ -336,6 +380,7 @@ void lo_march_1d_sub(const lo_molecule *m, int K, const double *R,
         double *a_norm = a_esc + (size_t)T * K;
         double *I = (double *)malloc(sizeof(double) * T * n_ch);
         double *phi = (double *)malloc(sizeof(double) * n_ch);
+        double *phl = m->hf_off ? (double *)malloc(sizeof(double) * (T + 1) * n_ch) : NULL;
         lo_seg1d *segs = (lo_seg1d *)malloc(sizeof(lo_seg1d) * 2 * (K + 1));
 #pragma omp for schedule(static)
         for (int j = 0; j < j_end; j++) {
@@ -361,11 +406,15 @@ void lo_march_1d_sub(const lo_molecule *m, int K, const double *R,
                 const int c = segs[i].cell;
                 const double sig = lo_sigma(sigma_turb[c], t_kin[c], m->mass_amu);
                 lo_profile(n_ch, v_min, dv, v[c] * segs[i].cosv, sig, phi);
+                if (phl)
+                    for (int t = 0; t < T; t++)
+                        lo_line_profile(m, t, n_ch, v_min, dv, v[c] * segs[i].cosv, sig, phi,
+                                        phl + (size_t)t * n_ch, phl + (size_t)T * n_ch);
                 const double w = (W[c] > 0.0) ? A * segs[i].s / W[c] : 0.0;
-                lo_step(T, n_ch, K, c, phi, segs[i].s, w, Kp, S, I, a_sij, a_esc, a_norm);
+                lo_step_lines(T, n_ch, K, c, phi, phl, segs[i].s, w, Kp, S, I, a_sij, a_esc, a_norm);
             }
         }
-        free(I); free(phi); free(segs);
+        free(I); free(phi); free(phl); free(segs);
     }
     for (int th = 0; th < nthr; th++) {
         const double *a = acc + (size_t)th * (2 * T + 1) * K;
@@ -678,6 +727,7 @@ void lo_spectra_1d(const lo_molecule *m, int line, int K, const double *R,
     for (int ip = 0; ip < n_p; ip++) {
         double *I = (double *)malloc(sizeof(double) * n_ch);
         double *phi = (double *)malloc(sizeof(double) * n_ch);
+        double *phl = (double *)malloc(sizeof(double) * 2 * n_ch);
         lo_seg1d *segs = (lo_seg1d *)malloc(sizeof(lo_seg1d) * 2 * (K + 1));
         for (int k = 0; k < n_ch; k++) I[k] = nbg;
         int n = lo_ray_segments_1d(K, R, p[ip], segs);
@@ -685,11 +735,12 @@ void lo_spectra_1d(const lo_molecule *m, int line, int K, const double *R,
             const int c = segs[i].cell;
             const double sig = lo_sigma(sigma_turb[c], t_kin[c], m->mass_amu);
             lo_profile(n_ch, v_min, dv, v[c] * segs[i].cosv, sig, phi);
+            lo_line_profile(m, line, n_ch, v_min, dv, v[c] * segs[i].cosv, sig, phi, phl, phl + n_ch);
             /* only line `line`: shift the parameter arrays to that row */
-            lo_step(1, n_ch, K, c, phi, segs[i].s, 0.0, Kp + (size_t)line * K, S + (size_t)line * K, I, NULL, NULL, NULL);
+            lo_step(1, n_ch, K, c, phl, segs[i].s, 0.0, Kp + (size_t)line * K, S + (size_t)line * K, I, NULL, NULL, NULL);
         }
         for (int k = 0; k < n_ch; k++) T_out[(size_t)ip * n_ch + k] = T0 * (I[k] - nbg);
-        free(I); free(phi); free(segs);
+        free(I); free(phi); free(phl); free(segs);
     }
     free(Kp); free(S);
 }
