@@ -142,6 +142,13 @@ typedef struct loc_model_desc {
  * frequency; collisional pairs u > l with a constant downward rate
  * coefficient k_ul (partner H2; upward rates follow from detailed balance).
  * 2 <= n_levels <= 32.
+ * Hyperfine structure (1D models, Sect. 2.1; NULL hf_n: none): hf_n[t]
+ * components of line t (0: the plain profile, at most 16), with velocity
+ * offsets hf_v (cm/s) and relative strengths hf_w (>= 0, summing to 1 per
+ * line within 1e-6), concatenated in line order.  The components are in
+ * LTE with each other: the line is one transition whose channel profile is
+ * the strength-weighted sum of the components' profiles, each shifted by
+ * its offset.  The channel band should hold every component.
  */
 typedef struct loc_molecule_desc {
     int n_levels;
@@ -154,6 +161,8 @@ typedef struct loc_molecule_desc {
     int n_coll;
     const int32_t *coll_u, *coll_l;
     const double *coll_k;
+    const int32_t *hf_n;
+    const double *hf_v, *hf_w;
 } loc_molecule_desc;
 
 /*

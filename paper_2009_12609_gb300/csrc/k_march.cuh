@@ -363,7 +363,11 @@ __device__ __forceinline__ int march_step_packed(const DevModel &m, const MarchA
 // the number of channels computed (0 for a skipped step).  pend carries the
 // lane's last compensated atomic from step to step (acc_flush after the
 // last step).
-template <int G, int ACC>
+// HF: the model's lines may have hyperfine components (1D): line t's
+// profile is the strength-weighted sum of its components' channel
+// fractions, each shifted by its offset, and the window widens to hold every
+// component; NORM keeps the unshifted profile.
+template <int G, int ACC, bool HF = false>
 __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a, float *I,
                                           const Step<G> &st, int lane, MarchState &pend)
 {
@@ -378,7 +382,21 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
     float u0, db;
     int klo, khi;
     step_window(m, a, st, u0, db, klo, khi);
-    if (khi - klo <= 16) return march_step_packed<G, ACC>(m, a, I, st, lane, klo, khi, u0, db, pend);
+    int hc0[HF ? G : 1], hc1[HF ? G : 1];
+    if constexpr (HF) {
+        if (a.window > 0.f) {
+            klo = max(0, klo + (int)floorf(m.hf_olo));
+            khi = min(nch, khi + (int)ceilf(m.hf_ohi));
+        }
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            hc0[t] = (t < a.n_lines) ? m.hf_off[a.line0 + t] : 0;
+            hc1[t] = (t < a.n_lines) ? m.hf_off[a.line0 + t + 1] : 0;
+        }
+        if (khi <= klo) return 0;
+    } else {
+        if (khi - klo <= 16) return march_step_packed<G, ACC>(m, a, I, st, lane, klo, khi, u0, db, pend);
+    }
     float Ks[G], Sv[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
@@ -398,6 +416,25 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
         const float e0 = 0.5f * erfcf(fabsf(b0));
         const float b1 = __shfl_down_sync(kFull, b0, 1);
         const float e1 = __shfl_down_sync(kFull, e0, 1);
+        float ph[HF ? G : 1];
+        if constexpr (HF) {
+            // every lane takes part in the components' shuffles
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                ph[t] = 0.f;
+                if (hc1[t] > hc0[t]) {
+                    float sum = 0.f;
+                    for (int c = hc0[t]; c < hc1[t]; c++) {
+                        const float bc = ((float)k + u0 - m.hf_o[c]) * db;
+                        const float ec = 0.5f * erfcf(fabsf(bc));
+                        const float bc1 = __shfl_down_sync(kFull, bc, 1);
+                        const float ec1 = __shfl_down_sync(kFull, ec, 1);
+                        sum += m.hf_w[c] * ((bc >= 0.f) ? (ec - ec1) : ((bc1 <= 0.f) ? (ec1 - ec) : (1.f - ec - ec1)));
+                    }
+                    ph[t] = sum;
+                }
+            }
+        }
         if (lane < 31 && k < khi) {
             const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
             nrm += phi;
@@ -405,7 +442,7 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
             if (full) {
 #pragma unroll
                 for (int t = 0; t < G; t++) {
-                    const float tm = one_minus_exp(Ks[t] * phi);
+                    const float tm = one_minus_exp(Ks[t] * ((HF && hc1[HF ? t : 0] > hc0[HF ? t : 0]) ? ph[HF ? t : 0] : phi));
                     const float iv = ip[t * nch];
                     sij[t] = fmaf(iv, tm, sij[t]);
                     esc[t] += tm;
@@ -415,7 +452,7 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
 #pragma unroll
                 for (int t = 0; t < G; t++) {
                     if (t < a.n_lines) {
-                        const float tm = one_minus_exp(Ks[t] * phi);
+                        const float tm = one_minus_exp(Ks[t] * ((HF && hc1[HF ? t : 0] > hc0[HF ? t : 0]) ? ph[HF ? t : 0] : phi));
                         const float iv = ip[t * nch];
                         sij[t] = fmaf(iv, tm, sij[t]);
                         esc[t] += tm;
@@ -543,13 +580,13 @@ __device__ __forceinline__ void sub_boundary(const DevModel &m, const MarchArgs 
     __syncwarp();
 }
 
-template <int G, int ACC>
+template <int G, int ACC, bool HF = false>
 __device__ __forceinline__ long long march_ray1d(const DevModel &m, const MarchArgs &a, float *I,
                                                  int j, int lane)
 {
     const int s0 = m.ray_off[j], n = m.ray_off[j + 1] - s0;
     MarchState pend = march_state();
-    auto fn = [&](const Step<G> &st) { return (long long)march_step<G, ACC>(m, a, I, st, lane, pend); };
+    auto fn = [&](const Step<G> &st) { return (long long)march_step<G, ACC, HF>(m, a, I, st, lane, pend); };
     long long nw = 0;
     const int outer = m.K - a.sub_k;                  // steps before the region (sub_k > 0)
     if (a.sub_k > 0 && a.sub_mode == 1) {

@@ -4,7 +4,7 @@
 
 namespace loc {
 
-template <int G, int ACC>
+template <int G, int ACC, bool HF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 11 ? 5 : 3) march1d_kernel(DevModel m, MarchArgs a0)
 {
     extern __shared__ float smem[];
@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, G <= 11 ? 5 : 3) march1d_
     const int j = (int)(item / a0.n_groups);
     const MarchArgs a = warp_args(m, a0, (int)(item - (long long)j * a0.n_groups));
     float *I = smem + (size_t)wid * a.per * m.n_ch;
-    const long long nw = march_ray1d<G, ACC>(m, a, I, j, lane);
+    const long long nw = march_ray1d<G, ACC, HF>(m, a, I, j, lane);
     flush_count(m, a, nw, lane);
 }
 
@@ -29,8 +29,10 @@ struct Launch1D {
         const size_t smem = (size_t)kWarpsPerBlock * a.per * m.n_ch * sizeof(float);
         const long long items = (long long)m.n_rays * a.n_groups;
         const long long nb = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        LOC_CUDA_TRY(cudaFuncSetAttribute(march1d_kernel<G, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        march1d_kernel<G, ACC><<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
+        // models with hyperfine lines take the kernel that evaluates them
+        auto k = m.hf_off ? march1d_kernel<G, ACC, true> : march1d_kernel<G, ACC, false>;
+        LOC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<(unsigned)nb, kWarpsPerBlock * 32, smem, st>>>(m, a);
         LOC_CUDA_TRY(cudaGetLastError());
         return LOC_OK;
     }
@@ -327,6 +329,7 @@ __global__ void spectra1d_kernel(DevModel m, int t, int n_p, const float4 *rec, 
     const int ch = (int)(item - (long long)ip * nchunk) * 31 + lane;
     const int n = nsteps[ip];
     const float4 *r = rec + (size_t)ip * 2 * m.K;
+    const int hc0 = m.hf_off ? m.hf_off[t] : 0, hc1 = m.hf_off ? m.hf_off[t + 1] : 0;
     float dI = 0.f;
     for (int b = 0; b < n; b += 32) {
         const float4 my = (b + lane < n) ? r[b + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -342,7 +345,17 @@ __global__ void spectra1d_kernel(DevModel m, int t, int n_p, const float4 *rec, 
             const float e0 = 0.5f * erfcf(fabsf(b0));
             const float b1 = __shfl_down_sync(kFull, b0, 1);
             const float e1 = __shfl_down_sync(kFull, e0, 1);
-            const float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
+            float phi = (b0 >= 0.f) ? (e0 - e1) : ((b1 <= 0.f) ? (e1 - e0) : (1.f - e0 - e1));
+            if (hc1 > hc0) {                 // hyperfine components of line t
+                phi = 0.f;
+                for (int c = hc0; c < hc1; c++) {
+                    const float bc = ((float)ch + u0 - m.hf_o[c]) * db;
+                    const float ec = 0.5f * erfcf(fabsf(bc));
+                    const float bc1 = __shfl_down_sync(kFull, bc, 1);
+                    const float ec1 = __shfl_down_sync(kFull, ec, 1);
+                    phi += m.hf_w[c] * ((bc >= 0.f) ? (ec - ec1) : ((bc1 <= 0.f) ? (ec1 - ec) : (1.f - ec - ec1)));
+                }
+            }
             const float tm = one_minus_exp(Ksv * phi);
             dI = fmaf(src - dI, tm, dI);
         }

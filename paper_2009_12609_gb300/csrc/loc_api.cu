@@ -437,6 +437,37 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
           "two lines join the same pair of levels");
     CHECK(distinct_level_pairs(mol->coll_u, mol->coll_l, mol->n_coll, L),
           "two collision entries join the same pair of levels");
+    // hyperfine components: offsets in channel units, per-line ranges
+    std::vector<int> hf_off;
+    std::vector<float> hf_o, hf_w;
+    float olo = 0.f, ohi = 0.f;
+    if (mol->hf_n) {
+        CHECK(D.geometry == LOC_SHELLS_1D, "hyperfine lines are supported for 1D models");
+        hf_off.assign(mol->n_lines + 1, 0);
+        int total = 0;
+        for (int t = 0; t < mol->n_lines; t++) {
+            CHECK(mol->hf_n[t] >= 0 && mol->hf_n[t] <= 16, "line %d: hyperfine components must be 0..16", t);
+            total += mol->hf_n[t];
+            hf_off[t + 1] = total;
+        }
+        CHECK(total == 0 || (mol->hf_v && mol->hf_w), "hyperfine offsets and strengths missing");
+        for (int t = 0; t < mol->n_lines; t++) {
+            double wsum = 0.0;
+            for (int c = hf_off[t]; c < hf_off[t + 1]; c++) {
+                CHECK(std::isfinite(mol->hf_v[c]) && std::isfinite(mol->hf_w[c]) && mol->hf_w[c] >= 0.0,
+                      "line %d: bad hyperfine component %d", t, c - hf_off[t]);
+                wsum += mol->hf_w[c];
+                const float o = (float)(mol->hf_v[c] / D.dv);
+                hf_o.push_back(o);
+                hf_w.push_back((float)mol->hf_w[c]);
+                olo = std::min(olo, o);
+                ohi = std::max(ohi, o);
+            }
+            CHECK(hf_off[t + 1] == hf_off[t] || fabs(wsum - 1.0) <= 1e-6,
+                  "line %d: hyperfine strengths sum to %g, not 1", t, wsum);
+        }
+        if (total == 0) hf_off.clear();
+    }
     D.L = L;
     D.T = mol->n_lines;
     D.P = mol->n_coll;
@@ -452,6 +483,15 @@ static loc_status set_molecule_impl(loc_model *m, const loc_molecule_desc *mol)
     TRY(upload(m, &D.coll_u, cu.data(), D.P, m->mol_mem, "coll_u"));
     TRY(upload(m, &D.coll_l, cl.data(), D.P, m->mol_mem, "coll_l"));
     TRY(upload(m, &D.coll_k, mol->coll_k, D.P, m->mol_mem, "coll_k"));
+    D.hf_off = nullptr;
+    D.hf_o = D.hf_w = nullptr;
+    D.hf_olo = olo;
+    D.hf_ohi = ohi;
+    if (!hf_off.empty()) {
+        TRY(upload(m, &D.hf_off, hf_off.data(), hf_off.size(), m->mol_mem, "hyperfine ranges"));
+        TRY(upload(m, &D.hf_o, hf_o.data(), hf_o.size(), m->mol_mem, "hyperfine offsets"));
+        TRY(upload(m, &D.hf_w, hf_w.data(), hf_w.size(), m->mol_mem, "hyperfine strengths"));
+    }
     const long long nc = D.n_cells;
     TRY(upload<float>(m, &D.nbg, nullptr, D.T, m->mol_mem, "nbg"));
     TRY(upload<double>(m, &D.nbg64, nullptr, D.T, m->mol_mem, "nbg64"));
@@ -581,6 +621,7 @@ static int steps_per_run(const loc_model *m, const loc_iter_opts *o, int per)
     const DevModel &D = m->d;
     if (D.geometry != LOC_SHELLS_1D) return 0;
     if (m->sub_k > 0) return 0;                  // sub-iterations march whole rays
+    if (D.hf_off) return 0;                      // so do hyperfine lines
     int c = o->steps_per_chunk != 0 ? o->steps_per_chunk : m->tuned_chunk;
     if (c < 0) return 0;
     if (c > 0) return c;

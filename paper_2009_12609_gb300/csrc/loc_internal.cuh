@@ -96,6 +96,9 @@ struct DevModel {
     int *coll_u, *coll_l;               // [P]
     double *coll_k;                     // [P]
     double2 *coll_rates;                // [n_cells][P] {C_ul, C_lu}, or null: computed in the solve
+    int *hf_off;                        // [T + 1] hyperfine components of each line (or null: none)
+    float *hf_o, *hf_w;                 // component offsets (channels, v / dv) and strengths
+    float hf_olo, hf_ohi;               // smallest (<= 0) and largest (>= 0) offset, channels
     float *nbg;                         // [T] background occupation
     double *nbg64;                      // [T]
 

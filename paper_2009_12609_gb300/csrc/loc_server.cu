@@ -517,6 +517,10 @@ loc_status loc_server_submit(loc_server *s, const loc_model_desc *d, const loc_m
         }
     }
     if (d->geometry != LOC_SHELLS_1D) { set_error("the server takes 1D models"); return LOC_EINVAL; }
+    if (mol->hf_n) {
+        for (int t = 0; t < mol->n_lines; t++)
+            if (mol->hf_n[t] != 0) { set_error("the server takes lines without hyperfine structure"); return LOC_EINVAL; }
+    }
     const int K = d->n_shells;
     if (K < 1 || K > 4096 || !d->radius || !d->v || !d->n_h2 || !d->t_kin || !d->sigma_turb || !d->abundance) {
         set_error("1D model: need 1 <= n_shells <= 4096 and all per-shell arrays");

@@ -65,7 +65,7 @@ class loc_molecule_desc(ctypes.Structure):
                 ("mass_amu", ctypes.c_double), ("n_lines", ctypes.c_int),
                 ("line_u", _i32), ("line_l", _i32), ("line_A", _d), ("line_nu", _d),
                 ("n_coll", ctypes.c_int), ("coll_u", _i32), ("coll_l", _i32),
-                ("coll_k", _d)]
+                ("coll_k", _d), ("hf_n", _i32), ("hf_v", _d), ("hf_w", _d)]
 
 
 class loc_iter_opts(ctypes.Structure):
@@ -299,6 +299,15 @@ def molecule_desc(mol, keep, n_levels=None):
     m.coll_u = keep(np.ascontiguousarray(cu[selc], np.int32)).ctypes.data_as(_i32)
     m.coll_l = keep(np.ascontiguousarray(cl[selc], np.int32)).ctypes.data_as(_i32)
     m.coll_k = _pd(keep(_f64(np.asarray(mol["coll_k"])[selc])))
+    if mol.get("hf_n") is not None:
+        # hyperfine components of the kept lines, in line order
+        n = np.asarray(mol["hf_n"], np.int64)
+        off = np.concatenate([[0], np.cumsum(n)])
+        idx = np.concatenate([np.arange(off[t], off[t + 1]) for t in np.flatnonzero(sel)] + [[]])
+        idx = idx.astype(np.int64)
+        m.hf_n = keep(np.ascontiguousarray(n[sel], np.int32)).ctypes.data_as(_i32)
+        m.hf_v = _pd(keep(_f64(np.asarray(mol["hf_v"], np.float64)[idx])))
+        m.hf_w = _pd(keep(_f64(np.asarray(mol["hf_w"], np.float64)[idx])))
     return m
 
 
