@@ -327,8 +327,10 @@ loc_status loc_get_radiation(const loc_model *m, double *sij, double *esc,
  * devices that marched disjoint direction ranges of the same model combine
  * by element-wise addition of each array (an all-reduce with sum), after
  * which loc_solve gives every device the populations of the whole ray
- * simulation.  Reading or writing them while the model's stream has work
- * queued races with that work. */
+ * simulation.  Octree leaves are in the library's storage order (depth
+ * first), the same on every device that holds the same model; the other
+ * calls of this interface use the level order.  Reading or writing them
+ * while the model's stream has work queued races with that work. */
 typedef struct loc_radiation_buffers_t {
     int64_t n_cells;
     int n_lines;

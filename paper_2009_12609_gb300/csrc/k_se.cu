@@ -275,7 +275,27 @@ __global__ void tex_kernel(DevModel m, int t, double *out)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m.n_cells) return;
-    out[c] = tex_of(m, t, m.x + c * m.L);
+    out[m.leaf_perm ? m.leaf_perm[c] : c] = tex_of(m, t, m.x + c * m.L);
+}
+
+__global__ void permute_rows_kernel(const int *perm, long long n, int w, const double *src, double *dst,
+                                    int to_api)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * w) return;
+    const long long i = idx / w, l = idx - i * w;
+    if (to_api) dst[(long long)perm[i] * w + l] = src[idx];
+    else dst[idx] = src[(long long)perm[i] * w + l];
+}
+
+loc_status launch_permute_rows(const int *perm, long long n, int w, const double *src, double *dst,
+                               int to_api, cudaStream_t st)
+{
+    const long long tot = n * w;
+    if (tot == 0) return LOC_OK;
+    permute_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(perm, n, w, src, dst, to_api);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
 }
 
 loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st)
@@ -319,15 +339,15 @@ __global__ void acc_to_f64_kernel(DevModel m, int fp64_acc, double *sij, double 
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)m.T * m.n_cells;
-    if (idx < n) {                               // idx = c * T + t -> out[t][c]
+    if (idx < n) {                               // idx = c * T + t -> out[t][c] (level order)
         const long long c = idx / m.T;
         const long long t = idx - c * m.T;
-        const long long o = t * m.n_cells + c;
+        const long long o = t * m.n_cells + (m.leaf_perm ? m.leaf_perm[c] : c);
         const double2 a = acc_value(m, idx, fp64_acc);
         if (sij) sij[o] = a.x;
         if (esc) esc[o] = a.y;
     }
-    if (idx < m.n_cells && norm) norm[idx] = norm_value(m, idx, fp64_acc);
+    if (idx < m.n_cells && norm) norm[m.leaf_perm ? m.leaf_perm[idx] : idx] = norm_value(m, idx, fp64_acc);
 }
 
 loc_status launch_acc_to_f64(const DevModel &m, int fp64_acc, double *sij, double *esc,

@@ -38,6 +38,7 @@ struct loc_model {
     std::vector<void *> geo_mem;     // lives as long as the model
     std::vector<void *> mol_mem;     // replaced by loc_set_molecule
     std::vector<int> oct_child, oct_leaf;       // octree index arrays (host copies)
+    std::vector<int> leaf_api;                  // octree: level-ordered index of each stored leaf
     std::vector<double> leaf_f[7];              // octree per-leaf fields (host staging)
     double *sigma_turb = nullptr;    // device copies kept for set_molecule
     double *vx = nullptr, *vy = nullptr, *vz = nullptr;
@@ -264,6 +265,32 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         }
         CHECK(nxt == D.n_tree, "refine flags describe %lld cells, octree_n_cells is %lld", nxt, (long long)D.n_tree);
         nc = nleaf;
+        // the leaves are stored depth first (root cells in raster order, the
+        // children of a refined cell in octant order): a ray's consecutive
+        // leaves, and the rays of neighbouring lattice lines, then touch
+        // nearby memory.  The interface keeps the level order: leaf_api maps
+        // a stored leaf to its level-ordered index.
+        m->leaf_api.assign(nleaf, 0);
+        {
+            std::vector<int> dfs(D.n_tree, -1);
+            long long next_id = 0;
+            std::vector<long long> stack;
+            for (long long r = N3 - 1; r >= 0; r--) stack.push_back(r);
+            while (!stack.empty()) {
+                const long long c = stack.back();
+                stack.pop_back();
+                if (m->oct_child[c] >= 0) {
+                    for (int o = 7; o >= 0; o--) stack.push_back(m->oct_child[c] + o);
+                } else {
+                    dfs[c] = (int)next_id++;
+                }
+            }
+            for (long long c = 0; c < D.n_tree; c++)
+                if (m->oct_leaf[c] >= 0) {
+                    m->leaf_api[dfs[c]] = m->oct_leaf[c];
+                    m->oct_leaf[c] = dfs[c];
+                }
+        }
         // per-leaf copies of the per-cell fields (values of refined cells are ignored)
         auto gather = [&](const double *src, std::vector<double> &dst) {
             dst.resize(nleaf);
@@ -329,6 +356,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
         if (oct) {
             TRY(upload(m, &D.child, m->oct_child.data(), D.n_tree, m->geo_mem, "octree children"));
             TRY(upload(m, &D.leaf_of, m->oct_leaf.data(), D.n_tree, m->geo_mem, "octree leaves"));
+            TRY(upload(m, &D.leaf_perm, m->leaf_api.data(), nc, m->geo_mem, "leaf order"));
             TRY(upload<int>(m, &D.oct_err, nullptr, 4, m->geo_mem, "octree flags"));
             LOC_CUDA_TRY(cudaMemsetAsync(D.oct_err, 0, 4 * sizeof(int), m->st));
             const size_t kid_n = (size_t)octree_persistent_warps(D) * 10 * kOctMaxKids;
@@ -1142,9 +1170,20 @@ loc_status loc_get_populations(const loc_model *m, double *out, size_t n_out)
     if (!m->has_mol) { set_error("no molecule"); return LOC_ESTATE; }
     const size_t n = (size_t)m->d.n_cells * m->d.L;
     if (n_out < n) { set_error("output needs %zu elements", n); return LOC_EINVAL; }
-    LOC_CUDA_TRY(cudaMemcpyAsync(out, m->d.x, sizeof(double) * n, cudaMemcpyDeviceToHost, m->st));
-    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
-    return LOC_OK;
+    if (!m->d.leaf_perm) {
+        LOC_CUDA_TRY(cudaMemcpyAsync(out, m->d.x, sizeof(double) * n, cudaMemcpyDeviceToHost, m->st));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        return LOC_OK;
+    }
+    double *buf = nullptr;                      // octree: stored order -> level order
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(double) * n));
+    loc_status s = launch_permute_rows(m->d.leaf_perm, m->d.n_cells, m->d.L, m->d.x, buf, 1, m->st);
+    cudaError_t e = cudaSuccess;
+    if (s == LOC_OK) e = cudaMemcpyAsync(out, buf, sizeof(double) * n, cudaMemcpyDeviceToHost, m->st);
+    if (s == LOC_OK && e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    cudaFree(buf);
+    return s;
 }
 
 loc_status loc_set_populations(loc_model *m, const double *in, size_t n_in)
@@ -1154,10 +1193,22 @@ loc_status loc_set_populations(loc_model *m, const double *in, size_t n_in)
     const size_t n = (size_t)m->d.n_cells * m->d.L;
     if (n_in != n) { set_error("populations need exactly %zu elements", n); return LOC_EINVAL; }
     if (!finite_pos(in, (long long)n, true)) { set_error("populations must be finite and >= 0"); return LOC_EINVAL; }
-    LOC_CUDA_TRY(cudaMemcpyAsync(m->d.x, in, sizeof(double) * n, cudaMemcpyHostToDevice, m->st));
-    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    if (!m->d.leaf_perm) {
+        LOC_CUDA_TRY(cudaMemcpyAsync(m->d.x, in, sizeof(double) * n, cudaMemcpyHostToDevice, m->st));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        m->has_rad = false;
+        return LOC_OK;
+    }
+    double *buf = nullptr;                      // octree: level order -> stored order
+    LOC_CUDA_TRY(cudaMalloc(&buf, sizeof(double) * n));
+    loc_status s = LOC_OK;
+    cudaError_t e = cudaMemcpyAsync(buf, in, sizeof(double) * n, cudaMemcpyHostToDevice, m->st);
+    if (e == cudaSuccess) s = launch_permute_rows(m->d.leaf_perm, m->d.n_cells, m->d.L, buf, m->d.x, 0, m->st);
+    if (e == cudaSuccess && s == LOC_OK) e = cudaStreamSynchronize(m->st);
+    if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+    cudaFree(buf);
     m->has_rad = false;
-    return LOC_OK;
+    return s;
 }
 
 loc_status loc_get_tex(const loc_model *m, int t, double *out, size_t n_out)
@@ -1327,6 +1378,7 @@ loc_status loc_trace_octree(const loc_model *mc, int dir, int64_t *out7, int64_t
         if (w > 0) {
             const cudaError_t e = cudaMemcpy(out7, buf, sizeof(long long) * 7 * w, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) { set_error("copy failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
+            else for (long long k = 0; k < w; k++) out7[7 * k + 5] = m->leaf_api[out7[7 * k + 5]];
         }
     }
     cudaFree(buf);
@@ -1351,6 +1403,10 @@ loc_status loc_octree_path_sums(const loc_model *mc, int dir, int64_t *out, size
     if (e != cudaSuccess) { set_error("path sums failed: %s", cudaGetErrorString(e)); s = LOC_ECUDA; }
     cudaFree(buf);
     if (s == LOC_OK) s = octree_status(m);
+    if (s == LOC_OK) {                          // stored order -> level order
+        std::vector<int64_t> tmp(out, out + m->d.n_cells);
+        for (long long i = 0; i < m->d.n_cells; i++) out[m->leaf_api[i]] = tmp[i];
+    }
     return s;
 }
 

@@ -84,6 +84,8 @@ struct DevModel {
     int4 *oct_kids;                     // per persistent warp: child lines
     int *oct_err;                       // device flag: frame capacity exceeded
     int *oct_order;                     // root-ray families, most work first (or null)
+    int *leaf_perm;                     // octree: [n_cells] level-ordered index of each leaf (the
+                                        // leaves are stored depth first; null for other geometries)
     unsigned long long *oct_rec;        // recorded paths of all families (or null: walk)
     long long *oct_rec_off;             // [families + 1] first record of each family
 
@@ -233,6 +235,10 @@ loc_status launch_coll_rates(const DevModel &m, double2 *out, cudaStream_t st);
 loc_status launch_bg(const DevModel &m, cudaStream_t st);
 loc_status launch_tex(const DevModel &m, int t, double *out_dev, cudaStream_t st);
 loc_status launch_dtex(const DevModel &m, const double *x0, cudaStream_t st);
+// rows of w doubles between the internal leaf order and the level order:
+// to_api = 1: dst[perm[i]] = src[i]; 0: dst[i] = src[perm[i]]
+loc_status launch_permute_rows(const int *perm, long long n, int w, const double *src, double *dst,
+                               int to_api, cudaStream_t st);
 loc_status launch_spectra1d(const DevModel &m, int t, const double *p_dev, int n_p, float4 *rec,
                             int *nsteps, float *T_dev, cudaStream_t st);
 loc_status launch_trace3d(const DevModel &m, int dir, long long i, long long j,
