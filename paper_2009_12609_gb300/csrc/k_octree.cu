@@ -283,14 +283,15 @@ struct OctTraceVisitor {
     unsigned long long *count;
     unsigned long long *sums;  // optional per-leaf sum of dz
     int dir;
-    unsigned local;            // active steps of the current family
+    unsigned local;            // active steps of the current family (added to *count
+                               // once per family when nothing is listed)
     unsigned ctrl;             // intensity copies (saves and loads) of the family
     __device__ void step(int lane, const OctLine &cur, long long dz, int leaf, int Lc)
     {
         local++;
         if (lane == 0) {
             if (sums) atomicAdd(sums + leaf, (unsigned long long)dz);
-            if (count) {
+            if (count && out) {                  // listing: one slot per step
                 const unsigned long long n = atomicAdd(count, 1ull);
                 if ((long long)n < cap) {
                     long long *o = out + 7 * n;
@@ -304,15 +305,25 @@ struct OctTraceVisitor {
     __device__ void load(int, int) { ctrl++; }
 };
 
-// Writes the path records of one family to rec[0 .. n).
+// Writes the path records of one family to rec[0 .. n).  Every lane calls
+// put with the same record; lane k keeps record k of the current block of
+// 32, and each full block is written by one coalesced store of the warp
+// (flush once more at the end of the family for a partial block).
 struct OctRecVisitor {
     static constexpr bool kNeedI = false;
     unsigned long long *rec;
     long long n, cap;
+    unsigned long long buf;
+    __device__ void flush(int lane)
+    {
+        const long long k = ((n - 1) & ~31ll) + lane;
+        if (k < n && k < cap) rec[k] = buf;
+    }
     __device__ void put(int lane, unsigned long long w)
     {
-        if (lane == 0 && n < cap) rec[n] = w;
+        if (lane == (int)(n & 31)) buf = w;
         n++;
+        if ((n & 31) == 0) flush(lane);
     }
     __device__ void step(int lane, const OctLine &, long long dz, int leaf, int Lc)
     {
@@ -546,14 +557,16 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) trace_octree_kernel(De
         vis.ctrl = 0;
         oct_traverse<1, kAccPlain>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
                         paths[wid], lane, vis, nw);
+        if (vis.count && !vis.out && lane == 0 && vis.local) atomicAdd(vis.count, (unsigned long long)vis.local);
         if (fam_work && lane == 0) fam_work[(long long)d * per_dir + r] = vis.local;
         if (fam_rec && lane == 0) fam_rec[(long long)d * per_dir + r] = vis.local + vis.ctrl;
     }
 }
 
 // Path records of every family f (direction f / N^2, root line f % N^2) at
-// m.oct_rec + m.oct_rec_off[f], by the traversal the march uses.  A family
-// whose record count differs from its slot raises error flag 4.
+// m.oct_rec + m.oct_rec_off[f], by the traversal the march uses; families
+// taken in decreasing order of work (m.oct_order) when it is known.  A
+// family whose record count differs from its slot raises error flag 4.
 __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) record_octree_kernel(DevModel m, unsigned *counter)
 {
     __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
@@ -572,16 +585,19 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) record_octree_kernel(D
         if (lane == 0) it = atomicAdd(counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if ((long long)it >= total) break;
-        const int d = (int)((long long)it / per_dir);
-        const long long r = (long long)it - (long long)d * per_dir;
+        const long long f = m.oct_order ? (long long)m.oct_order[it] : (long long)it;
+        const int d = (int)(f / per_dir);
+        const long long r = f - (long long)d * per_dir;
         g.D = m.dirs[d];
         OctRecVisitor vis;
-        const long long r0 = m.oct_rec_off[it];
+        const long long r0 = m.oct_rec_off[f];
         vis.rec = m.oct_rec + r0;
-        vis.cap = m.oct_rec_off[it + 1] - r0;
+        vis.cap = m.oct_rec_off[f + 1] - r0;
         vis.n = 0;
+        vis.buf = 0ull;
         oct_traverse<1, kAccPlain>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
                         paths[wid], lane, vis, nw);
+        if (vis.n & 31) vis.flush(lane);
         if (vis.n != vis.cap && lane == 0) atomicExch(m.oct_err, 4);
     }
 }
