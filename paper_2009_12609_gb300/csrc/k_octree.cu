@@ -603,6 +603,123 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) record_octree_kernel(D
 }
 
 // ----------------------------------------------------------------------------
+// Recording in one traversal.  The families' record counts are not known
+// before the walk, so each warp appends its family's records to chunks of
+// kPoolChunk records taken from a pool (one atomic per chunk, next[c] links
+// a family's chunks); the walk also yields the families' work and record
+// counts.  The host then lays the records out contiguously
+// (compact_octree_kernel).  A pool too small for the model raises flag 5
+// (the counts stay exact; the caller records again with the two-pass
+// scheme).
+// ----------------------------------------------------------------------------
+constexpr int kPoolChunk = (int)kOctPoolChunk;   // a multiple of 32
+
+struct OctPoolVisitor {
+    static constexpr bool kNeedI = false;
+    unsigned long long *pool;
+    int *next;
+    unsigned *chunks;           // chunks handed out so far
+    long long cap;              // chunks in the pool
+    int *err;
+    long long n;                // records of the family so far
+    unsigned steps;             // active steps of the family
+    long long chunk;            // current chunk (-1: none, the pool ran out)
+    long long head;             // first chunk of the family
+    unsigned long long buf;     // lane k: record k of the current block of 32
+    __device__ void flush(int lane)
+    {
+        const long long b = (n - 1) & ~31ll;            // first record of the block
+        if (chunk >= 0 && b + lane < n)
+            pool[(size_t)chunk * kPoolChunk + (size_t)(b & (kPoolChunk - 1)) + lane] = buf;
+    }
+    __device__ void put(int lane, unsigned long long w)
+    {
+        if ((n & (kPoolChunk - 1)) == 0) {
+            unsigned c = 0;
+            if (lane == 0) c = atomicAdd(chunks, 1u);
+            c = __shfl_sync(kFull, c, 0);
+            long long nc = (long long)c < cap ? (long long)c : -1;
+            if (nc < 0 && lane == 0) atomicExch(err, 5);
+            if (n == 0) head = nc;
+            else if (chunk >= 0 && lane == 0) next[chunk] = (int)nc;
+            if (chunk < 0 && n > 0) nc = -1;            // a broken chain stays broken
+            chunk = nc;
+        }
+        if (lane == (int)(n & 31)) buf = w;
+        n++;
+        if ((n & 31) == 0) flush(lane);
+    }
+    __device__ void step(int lane, const OctLine &, long long dz, int leaf, int Lc)
+    {
+        steps++;
+        put(lane, rec_step(leaf, dz, Lc));
+    }
+    __device__ void save(int lane, int depth) { put(lane, rec_ctrl(kRecSave, depth)); }
+    __device__ void load(int lane, int depth) { put(lane, rec_ctrl(kRecLoad, depth)); }
+};
+
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) pool_octree_kernel(DevModel m, unsigned *counter,
+                                                                              OctPoolVisitor v0,
+                                                                              unsigned *fam_work,
+                                                                              unsigned *fam_rec, int *fam_head)
+{
+    __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
+    __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kOctWarpsPerBlock + wid;
+    int4 *kids = m.oct_kids + (size_t)gw * kOctMaxDepth * kOctMaxKids;
+    const long long per_dir = (long long)m.N * m.N;
+    const MarchArgs a = oct_geo_args();
+    long long nw = 0;
+    OctGeo g = oct_geo(m);
+    const long long total = per_dir * m.n_dir;
+    while (true) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if ((long long)it >= total) break;
+        const int d = (int)((long long)it / per_dir);
+        const long long r = (long long)it - (long long)d * per_dir;
+        g.D = m.dirs[d];
+        OctPoolVisitor vis = v0;
+        vis.n = 0;
+        vis.steps = 0;
+        vis.chunk = -1;
+        vis.head = -1;
+        vis.buf = 0ull;
+        oct_traverse<1, kAccPlain>(m, a, g, (int)(r / m.N), (int)(r % m.N), nullptr, nullptr, kids, frames[wid],
+                        paths[wid], lane, vis, nw);
+        if (vis.n & 31) vis.flush(lane);
+        if (lane == 0) {
+            fam_work[it] = vis.steps;
+            fam_rec[it] = (unsigned)vis.n;
+            fam_head[it] = (int)vis.head;
+        }
+    }
+}
+
+// Copies family f's records from its pool chunks to m.oct_rec +
+// m.oct_rec_off[f] (one warp per family, coalesced loads and stores).
+__global__ void compact_octree_kernel(DevModel m, const unsigned long long *pool, const int *next,
+                                      const int *fam_head, long long fams)
+{
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long f = w0; f < fams; f += nwarps) {
+        const long long r0 = m.oct_rec_off[f], n = m.oct_rec_off[f + 1] - r0;
+        int c = fam_head[f];
+        for (long long k = 0; k < n && c >= 0; k += kPoolChunk) {
+            const unsigned long long *src = pool + (size_t)c * kPoolChunk;
+            const long long len = min((long long)kPoolChunk, n - k);
+            for (long long q = lane; q < len; q += 32) m.oct_rec[r0 + k + q] = src[q];
+            if (k + kPoolChunk < n) c = next[c];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Replay of the recorded paths: the march without the traversal.  A warp
 // takes (family, line group) items in decreasing order of work, streams the
 // family's records (32 per coalesced load, broadcast by shuffle) and applies
@@ -880,6 +997,35 @@ loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long 
     vis.ctrl = 0;
     const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
     trace_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, dir, vis, counter, fam_work, fam_rec);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *next, long long cap_chunks,
+                              unsigned *chunk_ctr, unsigned *fam_work, unsigned *fam_rec, int *fam_head,
+                              cudaStream_t st)
+{
+    unsigned *counter = (unsigned *)(m.oct_err + 1);
+    LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    LOC_CUDA_TRY(cudaMemsetAsync(chunk_ctr, 0, sizeof(unsigned), st));
+    OctPoolVisitor v;
+    memset(&v, 0, sizeof(v));
+    v.pool = pool;
+    v.next = next;
+    v.chunks = chunk_ctr;
+    v.cap = cap_chunks;
+    v.err = m.oct_err;
+    const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
+    pool_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, counter, v, fam_work, fam_rec, fam_head);
+    LOC_CUDA_TRY(cudaGetLastError());
+    return LOC_OK;
+}
+
+loc_status launch_compact_octree(const DevModel &m, const unsigned long long *pool, const int *next,
+                                 const int *fam_head, long long fams, cudaStream_t st)
+{
+    const long long blocks = std::min<long long>((fams + 7) / 8, (long long)octree_sms() * 16);
+    compact_octree_kernel<<<(unsigned)std::max(1ll, blocks), 256, 0, st>>>(m, pool, next, fam_head, fams);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

@@ -65,6 +65,7 @@ struct loc_model {
     std::vector<void *> oct_mem;
     long long path_records = 0;      // octree: recorded path records (0: the march walks the tree)
     std::vector<void *> path_mem;
+    std::vector<void *> tmp_mem;     // buffers of one call (the octree record pool)
     // 1D sub-iterations (set for the duration of a loc_iterate call)
     int sub_k = 0;                   // region: the sub_k innermost shells (0: none)
     int sub_mode = 0;                // 0: full march storing sub_I, 1: region march
@@ -147,10 +148,65 @@ const char *loc_last_error(void) { return g_err; }
 
 const char *loc_version(void) { return "loc-gb300 0.1 (sm_103a)"; }
 
+// Records of the path walk into a chunk pool (launch_pool_octree), kept
+// until they are laid out contiguously; the buffers are the model's tmp_mem.
+struct OctPool {
+    unsigned long long *pool = nullptr;
+    int *next = nullptr;
+    int *head = nullptr;
+};
+
+// One traversal of every family into a pool sized for about four records
+// per leaf and direction (measured clouds need 2.2) plus a partial chunk per
+// family, at most 40 % of the free device memory.  Fills fam_work and
+// fam_rec and sets ok when every record fit; ok == false (pool not
+// allocated, or too small) leaves the two-pass scheme to the caller.
+static loc_status pool_octree_paths(loc_model *m, long long fams, unsigned *work, unsigned *nrec, OctPool &P,
+                                    bool &ok)
+{
+    DevModel &D = m->d;
+    ok = false;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return LOC_OK;
+    }
+    const long long chunk_b = kOctPoolChunk * (long long)sizeof(unsigned long long) + (long long)sizeof(int);
+    long long cap = (4ll * D.n_cells * D.n_dir + kOctPoolChunk - 1) / kOctPoolChunk + fams;
+    cap = std::min(cap, (long long)(0.4 * (double)free_b) / chunk_b);
+    cap = std::min(cap, (long long)INT32_MAX);
+    if (cap < fams) return LOC_OK;
+    P.pool = (unsigned long long *)dev_alloc(m, (size_t)cap * kOctPoolChunk * sizeof(unsigned long long), m->tmp_mem);
+    P.next = (int *)dev_alloc(m, (size_t)cap * sizeof(int), m->tmp_mem);
+    P.head = (int *)dev_alloc(m, (size_t)fams * sizeof(int), m->tmp_mem);
+    unsigned *ctr = (unsigned *)dev_alloc(m, sizeof(unsigned), m->tmp_mem);
+    if (!P.pool || !P.next || !P.head || !ctr) {
+        dev_free_all(m, m->tmp_mem);
+        return LOC_OK;
+    }
+    TRY(launch_pool_octree(D, P.pool, P.next, cap, ctr, work, nrec, P.head, m->st));
+    int flag = 0;
+    LOC_CUDA_TRY(cudaMemcpyAsync(&flag, D.oct_err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+    if (flag == 5) {                                  // pool too small: counts exact, records not
+        LOC_CUDA_TRY(cudaMemsetAsync(D.oct_err, 0, sizeof(int), m->st));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        dev_free_all(m, m->tmp_mem);
+        return LOC_OK;
+    }
+    if (flag) {
+        set_error("tracing the octree paths failed (code %d)", flag);
+        return LOC_ECUDA;
+    }
+    ok = true;
+    return LOC_OK;
+}
+
 // Records of the octree paths (see record_octree_kernel): offsets from the
 // per-family record counts, one device buffer for all records, filled by one
-// traversal.  A failed allocation leaves the model walking the tree.
-static loc_status record_octree_paths(loc_model *m, const std::vector<unsigned> &nrec)
+// more traversal, or copied from the pool of pool_octree_paths when given.
+// A failed allocation leaves the model walking the tree.
+static loc_status record_octree_paths(loc_model *m, const std::vector<unsigned> &nrec, const OctPool *P = nullptr)
 {
     DevModel &D = m->d;
     const size_t fams = nrec.size();
@@ -171,7 +227,8 @@ static loc_status record_octree_paths(loc_model *m, const std::vector<unsigned> 
     LOC_CUDA_TRY(cudaMemcpyAsync(offd, off.data(), sizeof(long long) * (fams + 1), cudaMemcpyHostToDevice, m->st));
     D.oct_rec = rec;
     D.oct_rec_off = offd;
-    TRY(launch_record_octree(D, m->st));
+    if (P) TRY(launch_compact_octree(D, P->pool, P->next, P->head, (long long)fams, m->st));
+    else TRY(launch_record_octree(D, m->st));
     int flag = 0;
     LOC_CUDA_TRY(cudaMemcpyAsync(&flag, D.oct_err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
     LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
@@ -377,12 +434,25 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             unsigned *work = nullptr, *nrec = nullptr;
             TRY(upload<unsigned>(m, &work, nullptr, fams, m->geo_mem, "family work"));
             TRY(upload<unsigned>(m, &nrec, nullptr, fams, m->geo_mem, "family records"));
-            TRY(launch_trace_octree(D, -1, nullptr, 0, cnt, m->st, nullptr, work, nrec));
-            LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
-            LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+            // recording: one walk into a pool when it fits, else a counting
+            // walk here and a recording walk below
+            OctPool pool;
+            bool pooled = false;
+            if (d->octree_paths == 0) {
+                TRY(pool_octree_paths(m, fams, work, nrec, pool, pooled));
+            }
+            if (!pooled) {
+                TRY(launch_trace_octree(D, -1, nullptr, 0, cnt, m->st, nullptr, work, nrec));
+                LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
+                LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+            }
             std::vector<unsigned> wh(fams), rh(fams);
             LOC_CUDA_TRY(cudaMemcpy(wh.data(), work, sizeof(unsigned) * fams, cudaMemcpyDeviceToHost));
             LOC_CUDA_TRY(cudaMemcpy(rh.data(), nrec, sizeof(unsigned) * fams, cudaMemcpyDeviceToHost));
+            if (pooled) {
+                total = 0;
+                for (long long f = 0; f < fams; f++) total += wh[f];
+            }
             std::vector<int> order(fams);
             for (long long f = 0; f < fams; f++) order[f] = (int)f;
             std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wh[x] > wh[y]; });
@@ -392,7 +462,14 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             // intensity copy) and let every ray simulation replay them,
             // unless the caller asked to walk the tree or the records do not
             // fit in device memory
-            if (d->octree_paths == 0) TRY(record_octree_paths(m, rh));
+            if (d->octree_paths == 0) {
+                const loc_status rs = record_octree_paths(m, rh, pooled ? &pool : nullptr);
+                if (!m->tmp_mem.empty()) {
+                    cudaStreamSynchronize(m->st);
+                    dev_free_all(m, m->tmp_mem);
+                }
+                if (rs != LOC_OK) return rs;
+            }
         } else {
             TRY(launch_count3d(D, cnt, m->st));
             LOC_CUDA_TRY(cudaMemcpyAsync(&total, cnt, sizeof(total), cudaMemcpyDeviceToHost, m->st));
@@ -1423,6 +1500,7 @@ void loc_destroy(loc_model *m)
     cudaStreamSynchronize(m->st);
     dev_free_all(m, m->oct_mem);
     dev_free_all(m, m->path_mem);
+    dev_free_all(m, m->tmp_mem);
     dev_free_all(m, m->sub_mem);
     dev_free_all(m, m->run_mem);
     dev_free_all(m, m->run_ab_mem);

@@ -255,6 +255,14 @@ loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long 
                                unsigned long long *sums = nullptr, unsigned *fam_work = nullptr,
                                unsigned *fam_rec = nullptr);
 loc_status launch_record_octree(const DevModel &m, cudaStream_t st);
+// one traversal into a chunk pool (records, work and record counts per
+// family; flag 5 when the pool ran out), then the contiguous layout
+constexpr long long kOctPoolChunk = 256;
+loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *next, long long cap_chunks,
+                              unsigned *chunk_ctr, unsigned *fam_work, unsigned *fam_rec, int *fam_head,
+                              cudaStream_t st);
+loc_status launch_compact_octree(const DevModel &m, const unsigned long long *pool, const int *next,
+                                 const int *fam_head, long long fams, cudaStream_t st);
 int octree_persistent_warps(const DevModel &m);
 int octree_max_warps(const DevModel &m);
 loc_status launch_map_grid3d(const DevModel &m, int t, int dir, float *T_dev, cudaStream_t st);
