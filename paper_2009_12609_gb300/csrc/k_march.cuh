@@ -168,18 +168,27 @@ __device__ __forceinline__ void march_state_end(const DevModel &m, const MarchAr
 }
 
 // Sum of v[i] over the 32 lanes for all i at once; lane l receives the
-// total of index l (recursive halving: 31 shuffles for 32 values).
+// total of index l (recursive halving: 31 shuffles for 32 values).  LIVE
+// marks the indices that may be non-zero (the others are 0 in every lane):
+// a pair of indices that are both 0 everywhere stays 0 without a shuffle, so
+// a step with 2 G + 1 sums of a G-line group issues fewer shuffles; the sums
+// that are formed, and their order, do not change.
+template <unsigned LIVE = 0xffffffffu>
 __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane)
 {
+    unsigned live = LIVE;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
         const bool up = (lane & m) != 0;
 #pragma unroll
         for (int i = 0; i < m; i++) {
-            const float send = up ? v[i] : v[i + m];
-            const float keep = up ? v[i + m] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, m);
+            if (((live >> i) | (live >> (i + m))) & 1u) {
+                const float send = up ? v[i] : v[i + m];
+                const float keep = up ? v[i + m] : v[i];
+                v[i] = keep + __shfl_xor_sync(kFull, send, m);
+            }
         }
+        live = (live | (live >> m)) & ((1u << m) - 1u);
     }
     return v[0];
 }
@@ -397,10 +406,12 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
     } else {
         if (khi - klo <= 16) return march_step_packed<G, ACC>(m, a, I, st, lane, klo, khi, u0, db, pend);
     }
+    // lane t < n_lines: K s of its line, then broadcast to every lane
+    const float my_ks = step_ks(st.kl.x, st.s);
     float Ks[G], Sv[G], sij[G], esc[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
-        Ks[t] = step_ks(__shfl_sync(kFull, st.kl.x, t), st.s);
+        Ks[t] = __shfl_sync(kFull, my_ks, t);
         Sv[t] = __shfl_sync(kFull, st.kl.y, t);
         sij[t] = 0.f;
         esc[t] = 0.f;
@@ -491,14 +502,12 @@ __device__ __forceinline__ int march_step(const DevModel &m, const MarchArgs &a,
 #pragma unroll
         for (int t = 0; t < G; t++) { v[t] = sij[t]; v[16 + t] = esc[t]; }
         v[15] = nrm;
-        const float r = transpose_reduce32(v, lane);
+        constexpr unsigned kLines = (G >= 15) ? 0x7fffu : ((1u << G) - 1u);
+        const float r = transpose_reduce32<kLines | (1u << 15) | (kLines << 16)>(v, lane);
         my_sij = r;
         my_esc = __shfl_down_sync(kFull, r, 16);
         my_nrm = r;
     }
-    float my_ks = 1.f;
-#pragma unroll
-    for (int t = 0; t < G; t++) if (lane == t) my_ks = Ks[t];
     step_commit<G, ACC>(m, a, st.cell, my_ks, st.w, lane, my_sij, my_esc, my_nrm, pend);
     return khi - klo;
 }
@@ -625,10 +634,11 @@ __device__ __forceinline__ void affine_step(const DevModel &m, const MarchArgs &
     step_window(m, a, st, u0, db, klo, khi);
     klo = max(klo, tlo);
     khi = min(khi, thi);
+    const float my_ks = step_ks(st.kl.x, st.s);
     float Ks[G], Sv[G];
 #pragma unroll
     for (int t = 0; t < G; t++) {
-        Ks[t] = step_ks(__shfl_sync(kFull, st.kl.x, t), st.s);
+        Ks[t] = __shfl_sync(kFull, my_ks, t);
         Sv[t] = __shfl_sync(kFull, st.kl.y, t);
     }
     const bool full = (a.n_lines == G);
