@@ -110,7 +110,11 @@ typedef struct loc_allocator {
  *               in device memory, and every ray simulation replays them;
  *               1 walks the tree in every ray simulation (no records).  The
  *               results are the same either way: the replay applies the
- *               same steps, in the same order, as the walk.
+ *               same steps, in the same order, as the walk.  Recording
+ *               takes one traversal into a temporary pool of at most 40 %
+ *               of the free device memory, or, when the pool does not fit,
+ *               one traversal that counts and one that records; 2 asks for
+ *               the latter outright (same records).
  */
 typedef struct loc_model_desc {
     int geometry;

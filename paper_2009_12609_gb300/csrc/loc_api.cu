@@ -293,7 +293,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             CHECK(std::isfinite(n2) && fabs(n2 - 1.0) < 1e-6, "direction %d is not a unit vector", i);
         }
         CHECK(d->octree_levels >= 0 && d->octree_levels <= 10, "octree_levels must be in [0, 10]");
-        CHECK(d->octree_paths == 0 || d->octree_paths == 1, "octree_paths must be 0 or 1");
+        CHECK(d->octree_paths >= 0 && d->octree_paths <= 2, "octree_paths must be 0, 1 or 2");
         CHECK(d->octree_refine && d->vx && d->vy && d->vz, "octree model needs refine flags and velocities");
         const long long N3 = (long long)d->n_root * d->n_root * d->n_root;
         CHECK(d->octree_n_cells >= N3 && d->octree_n_cells < (1ll << 31), "octree_n_cells out of range");
@@ -438,6 +438,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             // walk here and a recording walk below
             OctPool pool;
             bool pooled = false;
+            const bool record = d->octree_paths != 1;
             if (d->octree_paths == 0) {
                 TRY(pool_octree_paths(m, fams, work, nrec, pool, pooled));
             }
@@ -462,7 +463,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             // intensity copy) and let every ray simulation replay them,
             // unless the caller asked to walk the tree or the records do not
             // fit in device memory
-            if (d->octree_paths == 0) {
+            if (record) {
                 const loc_status rs = record_octree_paths(m, rh, pooled ? &pool : nullptr);
                 if (!m->tmp_mem.empty()) {
                     cudaStreamSynchronize(m->st);

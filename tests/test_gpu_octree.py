@@ -206,6 +206,23 @@ def test_octree_replay_equals_walk(loc, oracle):
         np.testing.assert_allclose(a, b, rtol=2e-6, atol=1e-9 * np.abs(b).max())
 
 
+def test_octree_recorders_agree(loc):
+    """The one-walk recorder (a chunk pool, then the contiguous layout) and
+    the two-walk one (count, then record; octree_paths = 2) write the same
+    records: the same record count, and the replayed marches agree to FP32
+    atomic-ordering noise."""
+    mol = LI.rotor_molecule()
+    model = LI.octree_cloud(N=10)
+    out = {}
+    for paths in (0, 2):
+        with loc.Model(dict(model, octree_paths=paths), mol) as m:
+            rep = m.iterate(max_iter=1, window_sigmas=8.0, lines_per_pass=6)
+            out[paths] = (rep, m.radiation())
+    assert out[0][0]["path_records"] == out[2][0]["path_records"] > out[0][0]["segments"] > 0
+    for a, b in zip(out[0][1], out[2][1]):
+        np.testing.assert_allclose(a, b, rtol=2e-6, atol=1e-9 * np.abs(b).max())
+
+
 @pytest.fixture(scope="module")
 def bench_recipe_octree(oracle):
     """The bench's octree recipe (refined up to 5 levels where n > 8 x mean,
