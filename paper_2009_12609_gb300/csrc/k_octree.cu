@@ -36,9 +36,6 @@ constexpr int kOctWarpsPerBlock = 4;
 static_assert(kOctWarpsPerBlock <= kWarpsPerBlock, "march_step's per-warp tiles are sized for kWarpsPerBlock warps");
 constexpr int kOctBlocksPerSM = 4;
 constexpr int kOctMaxBlocksPerSM = 8;       // replay: up to 32 warps per SM
-// blocks per SM of the one-walk recorder (it holds no intensities; 6 and 8
-// blocks, at 80 and 64 registers with spills, walked slower than 4)
-constexpr int kOctWalkBlocksPerSM = 4;
 constexpr int kOctMaxDepth = 10;
 
 // floor(n / q) with minv = floor((2^64 - 1) / q): one correction step
@@ -661,7 +658,7 @@ struct OctPoolVisitor {
     __device__ void load(int lane, int depth) { put(lane, rec_ctrl(kRecLoad, depth)); }
 };
 
-__global__ void __launch_bounds__(kOctWarpsPerBlock * 32, kOctWalkBlocksPerSM) pool_octree_kernel(DevModel m, unsigned *counter,
+__global__ void __launch_bounds__(kOctWarpsPerBlock * 32) pool_octree_kernel(DevModel m, unsigned *counter,
                                                                               OctPoolVisitor v0,
                                                                               unsigned *fam_work,
                                                                               unsigned *fam_rec, int *fam_head)
@@ -931,12 +928,6 @@ int octree_persistent_warps(const DevModel &m)
     return octree_sms() * kOctBlocksPerSM * kOctWarpsPerBlock;
 }
 
-int octree_walk_warps(const DevModel &m)
-{
-    (void)m;
-    return octree_sms() * std::max(kOctBlocksPerSM, kOctWalkBlocksPerSM) * kOctWarpsPerBlock;
-}
-
 int octree_max_warps(const DevModel &m)
 {
     (void)m;
@@ -1024,7 +1015,7 @@ loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *
     v.chunks = chunk_ctr;
     v.cap = cap_chunks;
     v.err = m.oct_err;
-    const int blocks = octree_sms() * kOctWalkBlocksPerSM;
+    const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
     pool_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, counter, v, fam_work, fam_rec, fam_head);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;

@@ -416,7 +416,7 @@ static loc_status create_impl(loc_model *m, const loc_model_desc *d)
             TRY(upload(m, &D.leaf_perm, m->leaf_api.data(), nc, m->geo_mem, "leaf order"));
             TRY(upload<int>(m, &D.oct_err, nullptr, 4, m->geo_mem, "octree flags"));
             LOC_CUDA_TRY(cudaMemsetAsync(D.oct_err, 0, 4 * sizeof(int), m->st));
-            const size_t kid_n = (size_t)octree_walk_warps(D) * 10 * kOctMaxKids;
+            const size_t kid_n = (size_t)octree_persistent_warps(D) * 10 * kOctMaxKids;
             TRY(upload<int4>(m, &D.oct_kids, nullptr, kid_n, m->geo_mem, "octree frames"));
         }
         TRY(upload<float4>(m, &D.vel, nullptr, nc, m->geo_mem, "velocity records"));

@@ -264,7 +264,6 @@ loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *
 loc_status launch_compact_octree(const DevModel &m, const unsigned long long *pool, const int *next,
                                  const int *fam_head, long long fams, cudaStream_t st);
 int octree_persistent_warps(const DevModel &m);
-int octree_walk_warps(const DevModel &m);     // >= octree_persistent_warps: the kids frames
 int octree_max_warps(const DevModel &m);
 loc_status launch_map_grid3d(const DevModel &m, int t, int dir, float *T_dev, cudaStream_t st);
 loc_status launch_map_octree(const DevModel &m, int t, int dir, int lam, float *T_dev, cudaStream_t st);
