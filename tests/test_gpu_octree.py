@@ -264,3 +264,30 @@ def test_octree_bench_launch_shapes(loc, oracle, bench_recipe_octree, per):
         if sel.any():
             err = np.max(np.abs(tex[t][sel] / tref[t, sel] - 1.0))
             assert err < 1e-4, (t, err)
+
+
+def test_octree_full_size_one_direction(loc, oracle):
+    """The bench's full-size octree (64^3 root refined up to 5 levels:
+    7,929,328 leaves; 11 lines, 64 channels, 48 directions) at the bench's
+    launch shape (6 lines per warp, compensated FP32, 8-sigma window,
+    replayed paths): the ray simulation of one direction (dir_range) against
+    the oracle's march of that direction, every leaf's SIJ, ESC and NORM.
+    The oracle gets a model whose direction table holds that direction
+    alone, so its step weights carry 1 instead of 1/48 for the direction's
+    share: its sums are 48 times the device's."""
+    model = LI.octree_cloud(N=64)
+    mol = LI.rotor_molecule()
+    d = 5
+    n_dir = len(model["dirs"])
+    lm = oracle.leaf_model(model)
+    x0 = oracle.lte_populations(mol, lm["t_kin"])
+    Kp, S = oracle.line_params(mol, lm, x0)
+    rs, re_, rn = oracle.march_octree(mol, dict(model, dirs=np.asarray(model["dirs"])[d:d + 1]), Kp, S)
+    with loc.Model(model, mol) as m:
+        m.march(dir_range=(d, d + 1), window_sigmas=8.0, lines_per_pass=6)
+        sij, esc, norm = (np.asarray(a) * n_dir for a in m.radiation())
+    assert rn.min() > 0.0                           # every leaf is crossed in every direction
+    np.testing.assert_allclose(norm, rn, rtol=2e-5, atol=1e-7 * rn.max())
+    for t in range(len(mol["line_nu"])):
+        np.testing.assert_allclose(sij[t], rs[t], rtol=5e-5, atol=1e-6 * np.abs(rs[t]).max())
+        np.testing.assert_allclose(esc[t], re_[t], rtol=5e-5, atol=1e-6 * np.abs(re_[t]).max())
