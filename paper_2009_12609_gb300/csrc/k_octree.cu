@@ -658,10 +658,13 @@ struct OctPoolVisitor {
     __device__ void load(int lane, int depth) { put(lane, rec_ctrl(kRecLoad, depth)); }
 };
 
+// walk_order (or null): the families in the order to walk them (the
+// host's estimate of decreasing work, so that the longest walks start first)
 __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) pool_octree_kernel(DevModel m, unsigned *counter,
                                                                               OctPoolVisitor v0,
                                                                               unsigned *fam_work,
-                                                                              unsigned *fam_rec, int *fam_head)
+                                                                              unsigned *fam_rec, int *fam_head,
+                                                                              const int *walk_order)
 {
     __shared__ OctFrame frames[kOctWarpsPerBlock][kOctMaxDepth];
     __shared__ int paths[kOctWarpsPerBlock][kOctMaxDepth + 1];
@@ -679,8 +682,9 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) pool_octree_kernel(Dev
         if (lane == 0) it = atomicAdd(counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if ((long long)it >= total) break;
-        const int d = (int)((long long)it / per_dir);
-        const long long r = (long long)it - (long long)d * per_dir;
+        const long long f = walk_order ? (long long)walk_order[it] : (long long)it;
+        const int d = (int)(f / per_dir);
+        const long long r = f - (long long)d * per_dir;
         g.D = m.dirs[d];
         OctPoolVisitor vis = v0;
         vis.n = 0;
@@ -692,9 +696,9 @@ __global__ void __launch_bounds__(kOctWarpsPerBlock * 32) pool_octree_kernel(Dev
                         paths[wid], lane, vis, nw);
         if (vis.n & 31) vis.flush(lane);
         if (lane == 0) {
-            fam_work[it] = vis.steps;
-            fam_rec[it] = (unsigned)vis.n;
-            fam_head[it] = (int)vis.head;
+            fam_work[f] = vis.steps;
+            fam_rec[f] = (unsigned)vis.n;
+            fam_head[f] = (int)vis.head;
         }
     }
 }
@@ -1003,7 +1007,7 @@ loc_status launch_trace_octree(const DevModel &m, int dir, long long *out, long 
 
 loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *next, long long cap_chunks,
                               unsigned *chunk_ctr, unsigned *fam_work, unsigned *fam_rec, int *fam_head,
-                              cudaStream_t st)
+                              const int *walk_order, cudaStream_t st)
 {
     unsigned *counter = (unsigned *)(m.oct_err + 1);
     LOC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
@@ -1016,7 +1020,8 @@ loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *
     v.cap = cap_chunks;
     v.err = m.oct_err;
     const int blocks = octree_persistent_warps(m) / kOctWarpsPerBlock;
-    pool_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, counter, v, fam_work, fam_rec, fam_head);
+    pool_octree_kernel<<<blocks, kOctWarpsPerBlock * 32, 0, st>>>(m, counter, v, fam_work, fam_rec, fam_head,
+                                                                   walk_order);
     LOC_CUDA_TRY(cudaGetLastError());
     return LOC_OK;
 }

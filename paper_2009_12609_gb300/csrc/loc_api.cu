@@ -184,7 +184,65 @@ static loc_status pool_octree_paths(loc_model *m, long long fams, unsigned *work
         dev_free_all(m, m->tmp_mem);
         return LOC_OK;
     }
-    TRY(launch_pool_octree(D, P.pool, P.next, cap, ctr, work, nrec, P.head, m->st));
+    // walk order: families by decreasing estimated work, the leaves of the
+    // root cells their root line crosses (lateral drift at each root layer's
+    // centre, mirrored axes as the march mirrors them), so that the longest
+    // walks start first
+    int *order_d = nullptr;
+    {
+        const int N = D.N;
+        const long long per_dir = (long long)N * N;
+        std::vector<Dir3D> dirs(D.n_dir);
+        LOC_CUDA_TRY(cudaMemcpyAsync(dirs.data(), D.dirs, sizeof(Dir3D) * D.n_dir, cudaMemcpyDeviceToHost, m->st));
+        LOC_CUDA_TRY(cudaStreamSynchronize(m->st));
+        std::vector<long long> leaves(m->oct_child.size(), 1);
+        for (long long c = (long long)leaves.size() - 1; c >= 0; c--) {
+            const int ch = m->oct_child[c];
+            if (ch >= 0) {
+                long long n = 0;
+                for (int o = 0; o < 8; o++) n += leaves[ch + o];
+                leaves[c] = n;
+            }
+        }
+        std::vector<long long> est(fams, 0);
+        const double inv_one = 1.0 / (double)(1ll << kFixedBits);
+        const long long stride[3] = {1, N, (long long)N * N};
+        std::vector<int> sh_a(N), sh_b(N);
+        std::vector<long long> base(N);
+        for (int d = 0; d < D.n_dir; d++) {
+            const Dir3D &q = dirs[d];
+            const double sa = (double)q.qa * inv_one, sb = (double)q.qb * inv_one;   // slopes <= 1
+            for (int k = 0; k < N; k++) {
+                sh_a[k] = (int)std::floor(sa * (k + 0.5)) % N;
+                sh_b[k] = (int)std::floor(sb * (k + 0.5)) % N;
+                base[k] = (long long)(q.flip[q.m] ? N - 1 - k : k) * stride[q.m];
+            }
+            const long long step_a = q.flip[q.a] ? -stride[q.a] : stride[q.a];
+            const long long step_b = q.flip[q.b] ? -stride[q.b] : stride[q.b];
+            const long long org = (q.flip[q.a] ? (long long)(N - 1) * stride[q.a] : 0) +
+                                  (q.flip[q.b] ? (long long)(N - 1) * stride[q.b] : 0);
+            for (int i = 0; i < N; i++) {
+                for (int j = 0; j < N; j++) {
+                    long long w = 0;
+                    for (int k = 0; k < N; k++) {
+                        int xa = i + sh_a[k], xb = j + sh_b[k];
+                        if (xa >= N) xa -= N;
+                        if (xb >= N) xb -= N;
+                        w += leaves[base[k] + org + xa * step_a + xb * step_b];
+                    }
+                    est[d * per_dir + (long long)i * N + j] = w;
+                }
+            }
+        }
+        std::vector<int> order(fams);
+        for (long long f = 0; f < fams; f++) order[f] = (int)f;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return est[x] > est[y]; });
+        order_d = (int *)dev_alloc(m, sizeof(int) * (size_t)fams, m->tmp_mem);
+        if (order_d)
+            LOC_CUDA_TRY(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * (size_t)fams, cudaMemcpyHostToDevice,
+                                         m->st));
+    }
+    TRY(launch_pool_octree(D, P.pool, P.next, cap, ctr, work, nrec, P.head, order_d, m->st));
     int flag = 0;
     LOC_CUDA_TRY(cudaMemcpyAsync(&flag, D.oct_err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
     LOC_CUDA_TRY(cudaStreamSynchronize(m->st));

@@ -260,7 +260,7 @@ loc_status launch_record_octree(const DevModel &m, cudaStream_t st);
 constexpr long long kOctPoolChunk = 256;
 loc_status launch_pool_octree(const DevModel &m, unsigned long long *pool, int *next, long long cap_chunks,
                               unsigned *chunk_ctr, unsigned *fam_work, unsigned *fam_rec, int *fam_head,
-                              cudaStream_t st);
+                              const int *walk_order, cudaStream_t st);
 loc_status launch_compact_octree(const DevModel &m, const unsigned long long *pool, const int *next,
                                  const int *fam_head, long long fams, cudaStream_t st);
 int octree_persistent_warps(const DevModel &m);
