@@ -13,9 +13,18 @@
   the rays created at the refined cell's upstream face start with the
   intensity of the coarse ray at that face (uniform static medium -> slab
   formulas).
-Parity unpinned beyond these: the intensity given to side rays (rays that
-enter a refined cell through a side face) is our reading of the side-ray
-rule and has no independent closed form.
+* Split rays, oblique: a uniform absorber (S = 0) with a refined slab and a
+  doubly refined sub-slab crossed along every direction whose main axis is
+  the slab normal: each leaf's SIJ equals the mean of n_bg e^(-a z) over its
+  depths (new rays at the slab's face, their termination where it ends, the
+  resumed parent).
+* Side rays, bounded: in the same absorber on random trees, no leaf has less
+  than the exact field and none more than the field 2 h0 higher up, the
+  largest extrapolation the side-ray rule allows.
+Parity unpinned beyond these: the exact intensity given to side rays (rays
+that enter a refined cell through a side face) is our reading of the
+side-ray rule, which extrapolates the creating ray's intensity at the
+refined cell's upstream face (Sect. 2.2) and has no closed form.
 """
 import numpy as np
 import pytest
@@ -185,3 +194,142 @@ def test_split_rays_axis_aligned_closed_form(oracle):
             expect = jext(1.0 + 0.5 * cz, 0.5)    # entered at the refined cell's face (depth 1)
         assert SIJ[0, k] / NORM[k] == pytest.approx(expect, rel=1e-12)
         assert NORM[k] == pytest.approx(phi.sum(), rel=1e-13)
+
+
+def _leaf_boxes(model):
+    """Lower corner (cm, per axis) and size (cm) of every cell, from the
+    level-ordered refinement flags (root cell (z N + y) N + x; child octant
+    bits x = 1, y = 2, z = 4)."""
+    r = np.asarray(model["refine"])
+    N, h0 = model["n_root"], model["h0"]
+    nc = len(r)
+    lo = np.zeros((nc, 3))
+    size = np.zeros(nc)
+    for c in range(N ** 3):
+        lo[c] = (c % N * h0, (c // N) % N * h0, c // (N * N) * h0)
+        size[c] = h0
+    child = _children(model)
+    for c in range(nc):
+        if child[c] >= 0:
+            hh = size[c] / 2
+            for o in range(8):
+                k = child[c] + o
+                lo[k] = lo[c] + hh * np.array([o & 1, (o >> 1) & 1, (o >> 2) & 1])
+                size[k] = hh
+    return lo, size
+
+
+def _absorber_sij(model, mol, lo, size, Kt, phi, d, lead=0.0):
+    """Closed-form SIJ [line][leaf] of a static absorber without emission
+    crossed along d (one direction), if every line at main-axis depth z
+    carries n_bg e^(-a_k max(z - lead, 0)), a_k = K phi_k / |d_m| (lead = 0:
+    the exact field; lead > 0: the field of rays that started up to `lead`
+    deeper than the depth whose intensity they took).  With S = 0 a step's
+    I_in (1 - e^-tau) / tau is the step's mean intensity, and each leaf's
+    lateral square holds exactly one active lattice line at every depth of
+    the leaf (its main-axis path is exactly its size, pinned above), so SIJ
+    = sum_k phi_k x the mean of that field over the leaf's depths
+    [zL, zL + H]; for lead = 0, n_bg e^(-a_k zL) (1 - e^(-a_k H)) / (a_k H)."""
+    m = int(np.argmax(np.abs(d)))
+    width = model["n_root"] * model["h0"]
+    zL = (lo[:, m] if d[m] > 0 else width - lo[:, m] - size) - lead
+    z0 = np.maximum(zL, 0.0)[:, None]                       # attenuated part [z0, zL + H]
+    flat = (np.minimum(zL + size, 0.0) - np.minimum(zL, 0.0))[:, None]   # unattenuated part
+    Ha = np.maximum((zL + size)[:, None] - z0, 0.0)
+    nbg = 1.0 / np.expm1(H * np.asarray(mol["line_nu"]) / (KB * model["t_bg"]))
+    out = []
+    for t in range(len(Kt)):
+        a = Kt[t] * phi[None, :] / abs(d[m])                       # per cm of depth
+        aH = a * Ha
+        ratio = np.where(aH > 0, -np.expm1(-aH) / np.where(aH > 0, aH, 1.0), 1.0)
+        mean = nbg[t] * (flat + np.exp(-a * z0) * Ha * ratio) / size[:, None]
+        out.append((phi[None, :] * mean).sum(axis=1))
+    return np.array(out)
+
+
+def _absorber(model, mol):
+    """Static, isothermal version of `model` and the inputs of an absorber
+    without emission: K per line (peak depth 1.5 and 4 across the model),
+    S = 0; the channel fractions from scipy's erf."""
+    from scipy.special import erf
+    nc = len(model["refine"])
+    model = dict(model, t_kin=np.full(nc, 15.0), sigma_turb=np.full(nc, 0.2e5),
+                 vx=np.zeros(nc), vy=np.zeros(nc), vz=np.zeros(nc))
+    sig = np.sqrt(0.2e5 ** 2 + KB * 15.0 / (mol["mass_amu"] * AMU))
+    vk = model["v_min"] + (np.arange(model["n_ch"]) + 0.5) * model["dv"]
+    s2 = np.sqrt(2.0) * sig
+    phi = 0.5 * (erf((vk + 0.5 * model["dv"]) / s2) - erf((vk - 0.5 * model["dv"]) / s2))
+    T = len(mol["line_nu"])
+    Kt = np.array([1.5, 4.0])[:T] / (phi.max() * model["n_root"] * model["h0"])
+    n_leaf = len(oracle_leaves(model))
+    Kp = np.repeat(Kt[:, None], n_leaf, axis=1)
+    return model, Kt, phi, Kp, np.zeros_like(Kp)
+
+
+def oracle_leaves(model):
+    return np.flatnonzero(np.asarray(model["refine"]) == 0)
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_uniform_absorber_refined_slab_closed_form(oracle, N):
+    """Rays split at a refined region's upstream face, terminated where it
+    ends, and the resumed parent, pinned for oblique directions: a root
+    layer refined across the whole (laterally periodic) model, the lower
+    half of its children refined again, crossed along directions whose main
+    axis is the slab normal (no side faces to enter through, so every new
+    ray starts at the slab's upstream face).  Every leaf matches the
+    closed form of a uniform absorber to rounding."""
+    mol = LI.rotor_molecule(n_levels=3)
+    base = LI.small_octree(N=N, levels=1, refine_frac=0.3, n_ch=24)
+    nroot = N ** 3
+    lay = [c for c in range(nroot) if c // (N * N) == N - 1]          # top root layer
+    refine = np.zeros(nroot + 8 * len(lay) + 8 * 4 * len(lay), np.int32)
+    refine[lay] = 1
+    first = nroot
+    for k in range(len(lay)):
+        for o in range(4):                                              # child octants z = 0
+            refine[first + 8 * k + o] = 1
+    model = dict(base, levels=2, refine=refine, n_h2=np.full(len(refine), 1e4),
+                 abundance=np.full(len(refine), 1e-8))
+    model, Kt, phi, Kp, S = _absorber(model, mol)
+    lo, size = _leaf_boxes(model)
+    lf = oracle.leaves(model)
+    lo, size = lo[lf], size[lf]
+    assert set(np.round(size / model["h0"], 6)) == {1.0, 0.5, 0.25}
+    dirs = [d for d in LI.healpix_ring_directions(2) if np.argmax(np.abs(d)) == 2]
+    assert len(dirs) >= 8 and min(d[2] for d in dirs) < 0 < max(d[2] for d in dirs)
+    for d in dirs:
+        SIJ, ESC, NORM = oracle.march_octree(mol, dict(model, dirs=np.asarray(d)[None, :]), Kp, S)
+        np.testing.assert_allclose(NORM, phi.sum(), rtol=1e-13)
+        np.testing.assert_allclose(SIJ, _absorber_sij(model, mol, lo, size, Kt, phi, d), rtol=1e-10)
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 0.4), (3, 3, 0.35), (4, 2, 0.3)])
+def test_uniform_absorber_side_rays_bounded(oracle, shape):
+    """Side rays (rays started where a line enters a refined cell through a
+    side face) take the intensity the creating line had at the cell's
+    upstream face (Sect. 2.2: an extrapolation over less than the size of
+    the refined cell).  In a uniform absorber no ray can then carry more
+    attenuation than the exact field, and none less than the field 2 h0
+    higher up (n_bg e^(-a max(z - 2 h0, 0))): per leaf, the closed forms of
+    these two fields bound SIJ; the leaves that no side ray crosses meet
+    the lower bound, and the side rays of these trees raise others above
+    it (this bounds the rule; its exact value is our reading)."""
+    N, levels, frac = shape
+    mol = LI.rotor_molecule(n_levels=3)
+    model, Kt, phi, Kp, S = _absorber(LI.small_octree(N=N, levels=levels, refine_frac=frac, n_ch=24), mol)
+    lo, size = _leaf_boxes(model)
+    lf = oracle.leaves(model)
+    lo, size = lo[lf], size[lf]
+    exact_frac, raised = [], 0
+    for d in LI.healpix_ring_directions(2)[::5]:
+        SIJ, ESC, NORM = oracle.march_octree(mol, dict(model, dirs=np.asarray(d)[None, :]), Kp, S)
+        np.testing.assert_allclose(NORM, phi.sum(), rtol=1e-13)
+        lo_b = _absorber_sij(model, mol, lo, size, Kt, phi, d)
+        hi_b = _absorber_sij(model, mol, lo, size, Kt, phi, d, lead=2 * model["h0"])
+        assert np.all(SIJ >= lo_b * (1 - 1e-12))
+        assert np.all(SIJ <= hi_b * (1 + 1e-12))
+        eq = np.isclose(SIJ, lo_b, rtol=1e-10, atol=0).all(axis=0)
+        exact_frac.append(eq.mean())
+        raised += int((~eq).sum())
+    assert min(exact_frac) > 0.1 and raised > 0
