@@ -21,13 +21,13 @@
  *
  * Parity status: every function here is pinned by tests in tests/ against
  * closed forms, invariants or brute force (the per-cell line truncation by
- * tests/test_oracle_truncation.py), except two parts, parity unpinned:
- * the asymmetry of infall lines from excitation gradients (qualitative blue
- * asymmetry only; the Doppler geometry is pinned by a homologous-infall
- * closed form), and the exact intensity of octree side rays (bounded, not
- * fixed: in a uniform absorber they lie between the exact field and the
- * field 2 h0 higher up; the split rays at a refined cell's upstream face
- * are pinned exactly) -- see the test module docstrings.
+ * tests/test_oracle_truncation.py), except one part, parity unpinned: the
+ * exact intensity of octree side rays (bounded, not fixed: in a uniform
+ * absorber they lie between the exact field and the field 2 h0 higher up;
+ * the split rays at a refined cell's upstream face are pinned exactly) --
+ * see the test module docstrings.  The infall line of a cloud with an
+ * excitation gradient is pinned by its convergence to a fine numerical
+ * integration of the continuous model.
  */
 #include <math.h>
 #include <stdint.h>
