@@ -565,9 +565,7 @@ loc_status loc_create_model(loc_model **out, const loc_model_desc *d)
     }
     loc_status s = create_impl(m, d);
     if (s != LOC_OK) {
-        cudaStreamSynchronize(m->st);
-        dev_free_all(m, m->geo_mem);
-        delete m;
+        loc_destroy(m);               // every buffer list, not only the geometry
         return s;
     }
     *out = m;
