@@ -187,9 +187,12 @@ static loc_status pool_octree_paths(loc_model *m, long long fams, unsigned *work
     // walk order: families by decreasing estimated work, the leaves of the
     // root cells their root line crosses (lateral drift at each root layer's
     // centre, mirrored axes as the march mirrors them), so that the longest
-    // walks start first
+    // walks start first.  The estimate reads N^3 root cells per direction
+    // (70 ms of host time for a 64^3 root and 48 directions, but 1.3 s for
+    // 128^3 and 10 s for 255^3, strided); beyond 2^25 reads the families
+    // are walked in index order.
     int *order_d = nullptr;
-    {
+    if ((long long)D.N * D.N * D.N * D.n_dir <= (1ll << 25)) {
         const int N = D.N;
         const long long per_dir = (long long)N * N;
         std::vector<Dir3D> dirs(D.n_dir);
