@@ -319,9 +319,13 @@ loc_status loc_get_radiation(const loc_model *m, double *sij, double *esc,
                              double *norm, size_t n_out_lines_cells,
                              size_t n_out_cells);
 
-/* Device addresses of a model's per-cell accumulators, valid until the
- * model is destroyed (loc_set_molecule reallocates them).  All are DEVICE
- * pointers owned by the library:
+/* Device addresses of a model's per-cell accumulators (the sums SIJ, ESC
+ * and NORM of Sect. 2 over all ray steps; Sect. 2.2 makes the directions of
+ * one simulation independent), valid until the model is destroyed
+ * (loc_set_molecule reallocates them).  LOC_EINVAL for NULL arguments,
+ * LOC_ESTATE before loc_set_molecule (*out is cleared on success first).
+ * All are DEVICE pointers owned by the library, every one allocated by
+ * loc_set_molecule whatever the precision:
  *  acc, acc_c     [n_cells][n_lines][2] FP32 {SIJ, ESC} and the
  *                 compensation words of their additions (zero unless the
  *                 precision is LOC_FP32_MARCH);
