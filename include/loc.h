@@ -293,9 +293,13 @@ loc_status loc_iterate(loc_model *m, const loc_iter_opts *o, loc_iter_report *r)
  * iteration, Sect. 3.3.2) without re-uploading the molecule. */
 loc_status loc_reset_populations(loc_model *m);
 
-/* One ray simulation with the current populations, without the
- * equilibrium solve: fills the per-cell accumulators read by
- * loc_get_radiation (for step-by-step checks). */
+/* One ray simulation (Sect. 2) with the current populations, without the
+ * equilibrium solve: clears and fills the per-cell accumulators read by
+ * loc_get_radiation and loc_radiation_buffers.  For 3D models
+ * o->dir_begin / dir_end restrict it to that range of the direction table
+ * (one device's share; loc_solve then takes the summed accumulators).
+ * LOC_ESTATE before loc_set_molecule, LOC_EINVAL for invalid options, the
+ * octree flags' LOC_ECUDA if a traversal limit was hit. */
 loc_status loc_march(loc_model *m, const loc_iter_opts *o);
 
 /* Choose the launch shape of the march: the number of lines each warp
